@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the SET executor on one GB300 (or N replicas under torchrun).
+
+Workload (the headline configuration): 4096 scan jobs, each saxpy -> exclusive prefix sum ->
+max|S| over n = 65536 fp32 elements (x, y uniform [-1, 1), per-job a uniform [-2, 2)), 512 KiB
+copied in and 512 KiB + 32 B copied out per job, 8 lane streams, 8 host dispatch workers, work
+stealing.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
+launch, H2D copy, kernel, D2H copy, completion callback) until set_wait_all returns.
+
+Printed JSON line:
+  value        jobs/s with job inputs and outputs resident in HBM (SET_IO_DEVICE: the graphs'
+               copy nodes are device-to-device), whole job over all ranks
+  e2e          the same through the C ABI with pinned host buffers (SET_IO_HOST: H2D and D2H
+               copies on the NVLink-C2C link inside the timed region)
+  roofline     the dominant kernel (saxpy_scan_max) timed alone with CUDA events per launch over
+               a > L2 working set, against the measured HBM copy bandwidth
+  pipeline     the bound max(sum H2D / B_h2d, sum D2H / B_d2h, sum (H2D + D2H) / B_bidir,
+               jobs x isolated kernel time) from copy rates measured here, and e2e / bound
+  baselines    single-stream launch loop and the batch-synchronous fixed-stream graph executor
+               on the same jobs (pinned host buffers)
+  cpu_baseline the CPU oracle on the host cores over a bounded sample of the same jobs
+
+--impl reference times the CPU oracle alone (this paper has no released code; the oracle is the
+reference arm).  Inputs are larger than L2 (2 GiB per direction), so no flush is needed between
+steps.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "jobs/s, mean kernel gap (us), p99 latency vs batch-sync CUDA-graph baseline"
+UNIT = "jobs/s"
+N_ELEM = 65536
+JOB_IN = 8 * N_ELEM
+JOB_OUT = 8 * N_ELEM + 32
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["set", "reference"], default="set")
+    p.add_argument("--jobs", type=int, default=4096)
+    p.add_argument("--streams", type=int, default=8)
+    p.add_argument("--workers", type=int, default=8)
+    p.add_argument("--ring", type=int, default=2)
+    p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if _torch().cuda.is_available() else "gloo"
+            if backend == "nccl":
+                _torch().cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            if _torch().cuda.is_available():
+                self.pg.barrier(device_ids=[self.local])
+            else:
+                self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        t = _torch()
+        dev = "cuda" if t.cuda.is_available() else "cpu"
+        x = t.tensor([v], dtype=t.float64, device=dev)
+        self.pg.all_reduce(x, op=self.pg.ReduceOp.MAX)
+        return float(x.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def shard(njobs: int, rank: int):
+    """Job ids of one rank: every rank runs its own njobs jobs (weak scaling, no collective)."""
+    return range(rank * njobs, (rank + 1) * njobs)
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- the oracle (CPU baseline / reference)
+
+def oracle_rate(job_ids, cpu_seconds: float, threads: int, max_distinct: int = 512):
+    """CPU oracle jobs/s over a bounded sample: inputs are generated before timing (up to
+    max_distinct distinct jobs, cycled), then jobs run on `threads` host threads (ctypes drops the
+    GIL) until about cpu_seconds of CPU work or the whole workload is done."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import datagen
+    import oracle
+
+    oracle.lib()
+    inputs = [datagen.scan_job(j, n=N_ELEM) for j in job_ids[:max_distinct]]
+
+    def one(k):
+        a, xy = inputs[k % len(inputs)]
+        oracle.job_saxpy_scan_max(a, xy[:N_ELEM], xy[N_ELEM:])
+
+    t0 = time.perf_counter()
+    one(0)
+    per_job = time.perf_counter() - t0
+    n = max(threads, min(len(job_ids), int(cpu_seconds / max(per_job, 1e-6))))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(n)))
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args, d: Dist):
+    if d.rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    ids = list(shard(args.jobs, 0))
+    for _ in range(args.warmup):
+        oracle_rate(ids[:threads], 0.2, threads)
+    rates, total_jobs, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        r, n, dt = oracle_rate(ids, 4.0, threads)
+        rates.append(r)
+        total_jobs += n
+        total_t += dt
+    value = total_jobs / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64 inputs)",
+        "config": {"workload": "scan jobs (saxpy -> exclusive scan -> max|S|), n=65536 fp32, 4096 jobs",
+                   "jobs_per_step": args.jobs, "l2": "inputs > L2 (no flush needed)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{total_jobs} jobs over {args.steps} steps, each a bounded sample "
+                                   f"(about 4 s of CPU work) of the 4096-job workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- the SET executor arm
+
+class Workload:
+    """Pinned host and HBM-resident copies of every job of this rank, plus descriptors."""
+
+    def __init__(self, S, ids, device_index: int):
+        import numpy as np
+
+        import datagen
+        t = _torch()
+        self.ids = list(ids)
+        nj = len(self.ids)
+        self.h_in = t.empty(nj * JOB_IN, dtype=t.uint8, pin_memory=True)
+        self.h_out = t.zeros(nj * JOB_OUT, dtype=t.uint8, pin_memory=True)
+        hv = self.h_in.numpy().view(np.float32).reshape(nj, 2 * N_ELEM)
+        self.scalars = []
+        for k, j in enumerate(self.ids):
+            a, _ = datagen.scan_job(j, n=N_ELEM, out=hv[k])
+            self.scalars.append(a)
+        dev = f"cuda:{device_index}"
+        self.d_in = self.h_in.to(dev)
+        self.d_out = t.zeros(nj * JOB_OUT, dtype=t.uint8, device=dev)
+        self.descs_host = self._descs(S, self.h_in.data_ptr(), self.h_out.data_ptr())
+        self.descs_dev = self._descs(S, self.d_in.data_ptr(), self.d_out.data_ptr())
+
+    def _descs(self, S, in_base, out_base):
+        arr = (S.set_job_desc * len(self.ids))()
+        for k in range(len(self.ids)):
+            arr[k] = S.make_desc(S.SET_JOB_SAXPY_SCAN_MAX, (N_ELEM,), in_base + k * JOB_IN, out_base + k * JOB_OUT,
+                                 scalar=self.scalars[k])
+        return arr
+
+
+def run_step(S, ctx, descs, n):
+    done = ctypes.c_size_t()
+    S.check(S.set_submit_many(ctx, descs, n, None, ctypes.byref(done)), "set_submit_many", ctx)
+    S.check(S.set_wait_all(ctx, 600_000_000), "set_wait_all", ctx)
+
+
+def timed(S, ctx, descs, n, args, d: Dist):
+    t = _torch()
+    for _ in range(args.warmup):
+        run_step(S, ctx, descs, n)
+    S.set_reset_stats(ctx)
+    d.barrier()
+    t.cuda.synchronize()
+    e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run_step(S, ctx, descs, n)
+    e1.record()
+    t.cuda.synchronize()
+    d.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = S.set_stats_t()
+    S.set_stats(ctx, ctypes.byref(st))
+    return d.max(ms), st.as_dict()
+
+
+def copy_rates(device_index: int, job_bytes: int, streams: int, reps: int = 1024):
+    """Pinned copy rates (GB/s) at the job's own size, `streams` streams back to back:
+    H2D alone, D2H alone, and H2D + D2H together (total bytes both ways)."""
+    t = _torch()
+    dev = f"cuda:{device_index}"
+    hs = [t.empty(job_bytes, dtype=t.uint8, pin_memory=True) for _ in range(streams)]
+    ho = [t.empty(job_bytes, dtype=t.uint8, pin_memory=True) for _ in range(streams)]
+    ds = [t.empty(job_bytes, dtype=t.uint8, device=dev) for _ in range(streams)]
+    do = [t.empty(job_bytes, dtype=t.uint8, device=dev) for _ in range(streams)]
+    ss = [t.cuda.Stream() for _ in range(streams)]
+
+    def go(h2d: bool, d2h: bool):
+        t.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(reps):
+            i = r % streams
+            with t.cuda.stream(ss[i]):
+                if h2d:
+                    ds[i].copy_(hs[i], non_blocking=True)
+                if d2h:
+                    ho[i].copy_(do[i], non_blocking=True)
+        t.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    go(True, True)
+    b = reps * job_bytes / 1e9
+    return {"h2d_gbs": b / go(True, False), "d2h_gbs": b / go(False, True), "bidir_total_gbs": 2 * b / go(True, True)}
+
+
+def kernel_time(S, w: Workload, launches: int = 512):
+    """Average duration (us) of the saxpy_scan_max kernel launched alone per job, CUDA events
+    around each launch on the launching stream, inputs cycling over the > L2 resident set."""
+    t = _torch()
+    s = t.cuda.Stream()
+    scratch = t.zeros(S.set_job_scratch_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), dtype=t.uint8,
+                      device=w.d_in.device)
+    nj = len(w.ids)
+    evs = [(t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)) for _ in range(launches)]
+    with t.cuda.stream(s):
+        for k in range(32):
+            d = w.descs_dev[k % nj]
+            S.check(S.set_launch_job(ctypes.byref(d), d.in_, d.out, scratch.data_ptr(), k, 0, s.cuda_stream), "launch")
+        for k in range(launches):
+            d = w.descs_dev[(k * 7) % nj]
+            evs[k][0].record(s)
+            S.set_launch_job(ctypes.byref(d), d.in_, d.out, scratch.data_ptr(), k, 0, s.cuda_stream)
+            evs[k][1].record(s)
+    s.synchronize()
+    ts = [a.elapsed_time(b) * 1e3 for a, b in evs]
+    return statistics.mean(ts), statistics.median(ts)
+
+
+def run_set(args, d: Dist):
+    t = _torch()
+    import paper_2606_05495_gb300 as S
+
+    dev_index = d.local if t.cuda.is_available() else 0
+    t.cuda.set_device(dev_index)
+    w = Workload(S, shard(args.jobs, d.rank), dev_index)
+    nj = len(w.ids)
+    cfg = dict(num_streams=args.streams, num_workers=args.workers, slot_bytes=S.set_job_slot_bytes(
+        S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), ring_depth=args.ring, device=dev_index)
+
+    # value: inputs and outputs resident in HBM
+    ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
+    clocks = Clocks(dev_index)
+    ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d)
+    clk = clocks.stop()
+    S.set_destroy(ctx_dev)
+
+    # e2e: pinned host buffers, H2D/D2H inside the timed region
+    ctx = S.create(S.default_config(io_mode=S.SET_IO_HOST, **cfg))
+    ms_host, st_host = timed(S, ctx, w.descs_host, nj, args, d)
+    baselines = {}
+    if not args.no_baselines:
+        for name, kind in (("single_stream_loop", S.SET_BASE_SYNC), ("batch_sync_graph", S.SET_BASE_BATCH_SYNC)):
+            st = S.set_stats_t()
+            S.check(S.set_run_baseline(ctx, kind, w.descs_host, nj, ctypes.byref(st)), name, ctx)  # warm-up
+            runs = []
+            for _ in range(max(1, min(args.steps, 3))):
+                S.check(S.set_run_baseline(ctx, kind, w.descs_host, nj, ctypes.byref(st)), name, ctx)
+                runs.append(st.as_dict())
+            best = sorted(runs, key=lambda r: r["jobs_per_s"])[len(runs) // 2]
+            baselines[name] = {"jobs_per_s": best["jobs_per_s"], "p50_us": best["p50_us"], "p99_us": best["p99_us"],
+                               "streams": 1 if kind == S.SET_BASE_SYNC else args.streams}
+    S.set_destroy(ctx)
+
+    k_mean_us, k_med_us = kernel_time(S, w)
+    rates = copy_rates(dev_index, JOB_IN, args.streams)
+    world = d.world
+    value = world * nj / (ms_dev * 1e-3)
+    e2e = world * nj / (ms_host * 1e-3)
+
+    alg_bytes = 16 * N_ELEM + 32  # read x, y; write z, S; m + trailer
+    achieved = alg_bytes / (k_mean_us * 1e-6) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    t_h2d = nj * JOB_IN / (rates["h2d_gbs"] * 1e9)
+    t_d2h = nj * JOB_OUT / (rates["d2h_gbs"] * 1e9)
+    t_bi = nj * (JOB_IN + JOB_OUT) / (rates["bidir_total_gbs"] * 1e9)
+    t_sm = nj * k_mean_us * 1e-6
+    bound_s = max(t_h2d, t_d2h, t_bi, t_sm)
+    if d.rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_dev, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 inputs, resident before timing)",
+        "config": {"workload": "scan jobs (saxpy -> exclusive scan -> max|S|), n=65536 fp32, 4096 jobs per GPU",
+                   "jobs_per_step": nj * world, "streams": args.streams, "workers": args.workers,
+                   "ring_depth": args.ring, "steal": True, "io": "HBM-resident in/out (SET_IO_DEVICE)",
+                   "l2": "inputs 2 GiB > L2 per step (no flush needed)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
+                "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
+                "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
+                "steals": st_host["steals"]},
+        "gpu_launches": args.steps * nj * 1,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "saxpy_scan_max_kernel",
+                     "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
+                     "alg_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "pipeline": {"copy_rates_gbs": rates, "bound_jobs_per_s": nj / bound_s,
+                     "e2e_frac_of_bound": (nj / (ms_host * 1e-3)) / (nj / bound_s),
+                     "terms_ms": {"h2d": t_h2d * 1e3, "d2h": t_d2h * 1e3, "bidir": t_bi * 1e3, "sm": t_sm * 1e3}},
+        "p99_us": st_host["p99_us"], "mean_kernel_gap_us": None,
+        "baselines": baselines, "clocks": clk,
+    }
+    if not args.no_cpu:
+        threads = os.cpu_count() or 1
+        r, n, dt = oracle_rate(list(shard(args.jobs, 0)), 10.0, threads)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{n} scan jobs of the workload ({dt:.1f} s wall on {threads} threads)"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    d = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, d)
+        else:
+            run_set(args, d)
+    finally:
+        d.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * set.h -- C ABI of the stream-event-triggered (SET) job executor for one GB300 (sm_103a).
+ *
+ * The executor follows Sec. 4 of "SET: Stream-Event-Triggered Scheduling for Efficient CUDA
+ * Graph Pipelines" (Li, Huang, Ogras):
+ *   - a job is a reusable CUDA graph: H2D copy -> chain or DAG of stage kernels -> D2H copy,
+ *     with per-job arguments held as placeholders and updated at run time (Sec. 4.1);
+ *   - each lane (the paper's worker W_i, Sec. 4.2 "Scheduler Components") owns a stream and a
+ *     ring of slots; a slot is a pre-allocated device buffer M with one pre-instantiated graph
+ *     executable G per job type bound to it, so G touches only M (Sec. 4.1, 4.2);
+ *   - per-lane bounded job queues Q_i and a lock-free free-slot pool W_pool (Sec. 4.2);
+ *   - set_submit is the job submitter (Algorithm 1);
+ *   - host dispatch workers pop a free slot, take a job from the slot's lane queue or steal one
+ *     from lane (w+k) mod b, retarget it to the slot (UpdateGraphParams through
+ *     cudaGraphExecKernelNodeSetParams / cudaGraphExecMemcpyNodeSetParams1D), launch the graph
+ *     and chain a completion callback to it (Algorithm 2);
+ *   - the completion callback, run by the CUDA driver through cudaLaunchHostFunc after an event
+ *     recorded behind the graph, counts the job done and returns the slot to W_pool
+ *     (Algorithm 3).  The lane stream itself never waits on the host.
+ *
+ * Conventions (every function):
+ *   - The return value is the status; nothing throws across this boundary.
+ *   - A CUDA error inside a context is sticky: later calls on that context return SET_ECUDA and
+ *     set_last_error() gives the CUDA error text.
+ *   - Host input / output buffers belong to the caller and must stay valid until the job
+ *     completes.  With SET_IO_HOST they must be page-locked (cudaHostAlloc or a pinned torch
+ *     tensor); with SET_IO_DEVICE they must be device pointers of the context's GPU.
+ *   - Device memory of the slot pool belongs to the context, or to the caller when passed in
+ *     set_config.pool / pool_bytes (for example a torch tensor).
+ *   - Thread safety: set_submit, set_submit_many, set_wait_all and set_stats may be called from
+ *     any number of threads.  set_destroy must not race with any other call on the context.
+ */
+#ifndef SET_H_
+#define SET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct set_ctx set_ctx; /* opaque: streams, graph execs, slots, queues, threads */
+
+typedef enum {
+  SET_OK = 0,
+  SET_EINVAL = -1,     /* bad argument or descriptor (type, sizes, null pointer, pageable host memory) */
+  SET_ENOMEM = -2,     /* job does not fit a slot, or the slot pool cannot be allocated */
+  SET_EAGAIN = -3,     /* every lane queue is full and SET_F_NONBLOCK was given */
+  SET_ETIMEDOUT = -4,  /* a bounded wait ran out */
+  SET_ECUDA = -5,      /* CUDA runtime error; sticky for the context, text in set_last_error */
+  SET_ESHUTDOWN = -6,  /* the context is being destroyed */
+  SET_EDEVICE = -7     /* a device-side check failed for that job: a bounded wait gave up or the
+                          returned trailer did not carry the job's id and slot generation */
+} set_status;
+
+/* Job types and their payload layouts.  "in" and "out" are the bytes of the H2D and D2H copies.
+ * Every out ends with a 16-byte set_trailer written by the job's last kernel.
+ *
+ * SET_JOB_BLUR_HIST       dims = {W, H}, 1 <= W <= 2048, 1 <= H <= 65535.
+ *   in : uint8 image, H rows of W bytes.
+ *   out: blurred uint8 image (W*H bytes, o = floor(sum of the 9 edge-clamped neighbours / 9)),
+ *        zero pad to 16 bytes, uint32 hist[256] of the blurred image, trailer.
+ * SET_JOB_SAXPY_SCAN_MAX  dims = {n}, 1 <= n <= 2^26; scalar = a.
+ *   in : float x[n] followed by float y[n].
+ *   out: float z[n] (z_i = fmaf(a, x_i, y_i)), float S[n] (exclusive prefix sum of z, fp32),
+ *        float m (max_i |S_i|), 12 zero bytes, trailer.
+ * SET_JOB_IMG_SOBEL_HIST  dims = {W, H}, 1 <= W, H <= 4096.
+ *   in : interleaved RGB uint8, H rows of 3*W bytes.
+ *   out: Sobel uint8 image (W*H bytes) of gray -> 5x5 Gaussian -> Sobel, each stage clamping
+ *        its own input at the border, zero pad to 16 bytes, uint32 hist[256], trailer.
+ * SET_JOB_MLP_LN          dims = {m}, 1 <= m <= 256; shared[0] = W1, shared[1] = W2 (device).
+ *   in : bf16 x[m][1024].
+ *   out: float out[m][1024] = GELU(x W1^T) W2^T + LayerNorm(x), then the trailer.
+ *        W1 is bf16 [4096][1024], W2 bf16 [1024][4096] (out_features x in_features), both
+ *        device-resident and owned by the caller.  The job is a fork/join DAG.
+ */
+typedef enum {
+  SET_JOB_BLUR_HIST = 1,
+  SET_JOB_SAXPY_SCAN_MAX = 2,
+  SET_JOB_IMG_SOBEL_HIST = 3,
+  SET_JOB_MLP_LN = 4
+} set_job_type;
+
+#define SET_NUM_JOB_TYPES 4
+
+/* set_job_desc.flags */
+#define SET_F_NONBLOCK 0x1u /* set_submit returns SET_EAGAIN instead of waiting for queue room */
+
+/* The last 16 bytes of every job's output. */
+typedef struct {
+  uint64_t job_id;   /* id set_submit returned for this job */
+  uint32_t slot_gen; /* generation of the slot that ran it (bumped at each completion) */
+  uint32_t word;     /* (SET_TRAILER_MAGIC << 16) | device error bits */
+} set_trailer;
+
+#define SET_TRAILER_MAGIC 0x5E7Cu
+#define SET_DEVERR_WAIT 0x1u /* a bounded device-side wait gave up */
+
+typedef struct {
+  uint32_t type;          /* set_job_type */
+  uint32_t flags;         /* SET_F_* */
+  const void* in;         /* caller-owned input (pinned host, or device with SET_IO_DEVICE) */
+  size_t in_bytes;        /* must equal set_job_in_bytes(type, dims) */
+  void* out;              /* caller-owned output, written only by the D2H copy */
+  size_t out_bytes;       /* must equal set_job_out_bytes(type, dims) */
+  uint32_t dims[4];       /* per type, see above; unused entries 0 */
+  float scalar;           /* SET_JOB_SAXPY_SCAN_MAX: a */
+  uint32_t reserved;      /* 0 */
+  const void* shared[2];  /* SET_JOB_MLP_LN: device W1, W2; otherwise NULL */
+  uint64_t user_tag;      /* opaque, kept with the job */
+  uint64_t t_arrival_ns;  /* arrival time (CLOCK_MONOTONIC ns) latency is measured from; 0 = at submit */
+  volatile int32_t* status; /* optional: set to a set_status when the job completes */
+} set_job_desc;
+
+/* Input / output placement of every job of a context. */
+typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1 } set_io_mode;
+
+typedef struct {
+  int num_streams;     /* lanes b (paper's workers), >= 1 */
+  int num_workers;     /* host dispatch threads, >= 1 */
+  size_t slot_bytes;   /* bytes per slot: must cover in + out + scratch of the largest job */
+  int ring_depth;      /* slots per lane (default 2): jobs a lane may hold in flight */
+  int queue_capacity;  /* per-lane job queue capacity (default 4, rounded up to a power of 2) */
+  int steal;           /* 1 (default): FindJob steals from other lanes; 0: local queue only */
+  int io_mode;         /* set_io_mode of every job */
+  int img_fused;       /* 1 (default): image jobs run one fused stencil kernel; 0: per stage */
+  void* pool;          /* optional caller-owned device memory for the slots (else cudaMalloc) */
+  size_t pool_bytes;   /* its size: >= num_streams * ring_depth * slot_bytes */
+  uint32_t type_mask;  /* bit (1 << type) per job type to instantiate graphs for; 0 = all */
+  int device;          /* CUDA device ordinal (default 0) */
+  int drain_timeout_ms; /* set_destroy waits at most this long for jobs in flight (default 30000) */
+} set_config;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t steals;          /* jobs launched by a lane other than the one they were queued on */
+  uint64_t updates;         /* graph parameter updates issued (node calls) */
+  uint64_t canary_errors;   /* trailers that did not match the job (should be 0) */
+  double elapsed_s;         /* first submit to last completion */
+  double jobs_per_s;        /* completed / elapsed_s */
+  double p50_us, p99_us, max_us; /* submit -> completion callback latency */
+  double mean_update_us;    /* host time of UpdateGraphParams per job */
+  double mean_launch_us;    /* host time of graph launch + callback chaining per job */
+} set_stats_t;
+
+/* ---- sizes ---- */
+
+/* Bytes of the H2D payload, the D2H payload (with trailer) and the device scratch of one job;
+ * 0 if type or dims are invalid.  Cf. Sec. 4.1: slots are sized once and reused. */
+size_t set_job_in_bytes(uint32_t type, const uint32_t dims[4]);
+size_t set_job_out_bytes(uint32_t type, const uint32_t dims[4]);
+size_t set_job_scratch_bytes(uint32_t type, const uint32_t dims[4]);
+/* Slot bytes one job needs: in + out + scratch, each rounded up to 256 bytes. */
+size_t set_job_slot_bytes(uint32_t type, const uint32_t dims[4]);
+
+/* ---- executor (Sec. 4.2, Algorithms 1-3) ---- */
+
+/* Defaults for every set_config field (num_streams 2, num_workers 2, ring 2, queue 4, ...). */
+void set_config_default(set_config* cfg);
+
+/* Initialization (Sec. 4.2): allocate the slot pool, create one stream per lane, instantiate
+ * one graph per (slot, job type), fill W_pool with every slot and start num_workers dispatch
+ * threads.  *out receives the context.  SET_ENOMEM if the pool cannot be allocated. */
+set_status set_create(int num_streams, int num_workers, size_t slot_bytes, set_ctx** out);
+set_status set_create_ex(const set_config* cfg, set_ctx** out);
+
+/* Job submitter (Algorithm 1): validate, claim the next id, push to the shortest non-full lane
+ * queue (lowest index on ties).  Blocks while every queue is full unless SET_F_NONBLOCK.
+ * *job_id (may be NULL) receives the id echoed in the trailer. */
+set_status set_submit(set_ctx* ctx, const set_job_desc* job, uint64_t* job_id);
+
+/* Submits n jobs in order (same rules as set_submit, one call across the boundary).
+ * *first_id receives the first id; ids are consecutive only if nothing else submits
+ * concurrently.  Returns at the first failure with *n_done (may be NULL) = jobs submitted. */
+set_status set_submit_many(set_ctx* ctx, const set_job_desc* jobs, size_t n, uint64_t* first_id,
+                           size_t* n_done);
+
+/* Waits until every submitted job has completed (completion counter == submitted counter).
+ * timeout_us < 0 waits forever.  SET_ETIMEDOUT if the time runs out. */
+set_status set_wait_all(set_ctx* ctx, int64_t timeout_us);
+
+/* Snapshot of the counters and the latency histogram (log buckets, 1/64 octave). */
+set_status set_stats(set_ctx* ctx, set_stats_t* out);
+
+/* Clears the counters, latencies and elapsed-time origin (not the job id counter). */
+set_status set_reset_stats(set_ctx* ctx);
+
+/* Drains (at most drain_timeout_ms for jobs still in flight), joins the worker threads, destroys
+ * graphs, streams and (if owned) the pool. */
+set_status set_destroy(set_ctx* ctx);
+
+/* Last error text of the context (or of the calling thread's last context-less call when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* set_last_error(set_ctx* ctx);
+
+/* ---- direct launches (no graph, no executor) ---- */
+
+/* Launches the stage kernels of one job on `stream` (a cudaStream_t, NULL = legacy default)
+ * over device buffers: d_in (in_bytes), d_out (out_bytes), d_scratch (scratch_bytes, zeroed
+ * once before its first use; every launch leaves it ready for the next one).  `job_id` and
+ * `slot_gen` go into the trailer.  Launches that share a scratch buffer must be ordered (same
+ * stream or event-chained).  Used by the single-stream baseline and for kernel timing. */
+set_status set_launch_job(const set_job_desc* job, const void* d_in, void* d_out, void* d_scratch,
+                          uint64_t job_id, uint32_t slot_gen, void* stream);
+
+/* Number of kernels set_launch_job launches for this job (graph kernel nodes per job). */
+int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused);
+
+/* ---- baselines run on the same kernels (Sec. 5.1.3) ---- */
+
+typedef enum {
+  SET_BASE_SYNC = 1,        /* synchronous model: one stream, copies and kernels one by one */
+  SET_BASE_BATCH_SYNC = 2   /* static batching: b streams with one graph exec each; per batch
+                               update b execs, launch b, synchronise every stream, repeat */
+} set_baseline_kind;
+
+/* Runs all n jobs under a baseline model with the context's lanes, slots and graph execs (the
+ * context's own dispatch threads stay idle).  Fills *out like set_stats. */
+set_status set_run_baseline(set_ctx* ctx, int kind, const set_job_desc* jobs, size_t n,
+                            set_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SET_H_ */

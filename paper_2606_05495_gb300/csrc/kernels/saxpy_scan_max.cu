@@ -1,0 +1,264 @@
+// saxpy_scan_max.cu -- scan job: z = fmaf(a, x, y), S = exclusive prefix sum of z, m = max|S_i|,
+// in one single-pass kernel.
+//
+// Tiles of 4096 elements (256 threads x 16 contiguous elements, 16-byte loads and stores).
+// Tiles take a ticket from an atomic counter so that tile ids follow scheduling order, and
+// resolve their prefix with decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", 2016): each tile publishes its aggregate, then walks back over
+// predecessors' status words until it meets an inclusive prefix.  Inside a tile the scan is
+// thread-serial, then warp-shuffle, then across the 8 warps.  Each tile also publishes its
+// max|S|; the last tile to finish (done counter) reduces them into m and writes the trailer.
+//
+// Scratch: a 64-byte header {ticket, done, epoch, err} followed by one 64-bit status word and
+// one float per tile.  Status words carry the header's epoch, so stale words of an earlier
+// launch never match; the last tile resets ticket/done/err and bumps the epoch, which leaves the
+// scratch ready for the next launch without any zeroing pass.  Every wait is bounded: a tile
+// that gives up sets SET_DEVERR_WAIT in the header, which the trailer reports.
+#include "stages.h"
+
+namespace setk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kPer = 16;
+constexpr int kTile = kThreads * kPer;
+static_assert(kTile == (int)kScanTile, "tile size shared with the layout code");
+constexpr int kSpinLimit = 1 << 22;  // ~0.1-0.4 s with the back-off below
+
+constexpr uint32_t kFlagAgg = 1, kFlagInc = 2;
+
+struct ScanHdr {
+  uint32_t ticket, done, epoch, err;
+  uint32_t pad[12];
+};
+static_assert(sizeof(ScanHdr) == kScanHdrBytes, "scan header size shared with the layout code");
+
+struct ScanArgs {
+  const float* x;
+  const float* y;
+  float* z;
+  float* S;
+  float* m_out;  // followed by 12 zero bytes
+  set_trailer* trailer;
+  uint8_t* scratch;
+  uint64_t job_id;
+  uint32_t n, T;
+  float a;
+  uint32_t slot_gen;
+};
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t status_word(uint32_t epoch, uint32_t flag, float v) {
+  return ((uint64_t)(epoch & 0x3FFFFFFFu) << 34) | ((uint64_t)flag << 32) | (uint64_t)__float_as_uint(v);
+}
+
+__global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs p) {
+  __shared__ uint32_t s_tile, s_epoch, s_last;
+  __shared__ float s_wsum[kWarps], s_wexcl[kWarps], s_wmax[kWarps];
+  __shared__ float s_prefix, s_agg;
+  ScanHdr* hdr = reinterpret_cast<ScanHdr*>(p.scratch);
+  uint64_t* status = reinterpret_cast<uint64_t*>(p.scratch + sizeof(ScanHdr));
+  float* tmax = reinterpret_cast<float*>(status + p.T);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) {
+    s_tile = atomicAdd(&hdr->ticket, 1u);
+    s_epoch = *reinterpret_cast<volatile uint32_t*>(&hdr->epoch) & 0x3FFFFFFFu;
+  }
+  __syncthreads();
+  const uint32_t tile = s_tile, epoch = s_epoch;
+  const uint32_t n = p.n;
+  const size_t base = (size_t)tile * kTile + (size_t)tid * kPer;
+  const bool vec = (n & 3u) == 0 && base + kPer <= n;
+
+  // saxpy: z = fmaf(a, x, y), written once
+  float z[kPer];
+  if (vec) {
+#pragma unroll
+    for (int q = 0; q < kPer / 4; ++q) {
+      const float4 xv = __ldg(reinterpret_cast<const float4*>(p.x + base) + q);
+      const float4 yv = __ldg(reinterpret_cast<const float4*>(p.y + base) + q);
+      z[4 * q + 0] = fmaf(p.a, xv.x, yv.x);
+      z[4 * q + 1] = fmaf(p.a, xv.y, yv.y);
+      z[4 * q + 2] = fmaf(p.a, xv.z, yv.z);
+      z[4 * q + 3] = fmaf(p.a, xv.w, yv.w);
+      reinterpret_cast<float4*>(p.z + base)[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const size_t i = base + k;
+      z[k] = 0.f;
+      if (i < n) {
+        z[k] = fmaf(p.a, p.x[i], p.y[i]);
+        p.z[i] = z[k];
+      }
+    }
+  }
+
+  // thread-serial exclusive scan of the thread's 16 elements
+  float e[kPer];
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    e[k] = acc;
+    acc += z[k];
+  }
+  // warp: inclusive shuffle scan of thread totals, exclusive by one more shuffle
+  float inc = acc;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float t = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+    if (lane >= off) inc += t;
+  }
+  float lane_excl = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+  if (lane == 0) lane_excl = 0.f;
+  if (lane == 31) s_wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const float w = lane < kWarps ? s_wsum[lane] : 0.f;
+    float wi = w;
+#pragma unroll
+    for (int off = 1; off < kWarps; off <<= 1) {
+      const float t = __shfl_up_sync(0xFFFFFFFFu, wi, off);
+      if (lane >= off) wi += t;
+    }
+    float we = __shfl_up_sync(0xFFFFFFFFu, wi, 1);
+    if (lane == 0) we = 0.f;
+    if (lane < kWarps) s_wexcl[lane] = we;
+    if (lane == kWarps - 1) s_agg = wi;
+  }
+  __syncthreads();
+
+  // decoupled look-back across tiles (one thread)
+  if (tid == 0) {
+    const float agg = s_agg;
+    float prefix = 0.f;
+    if (tile == 0) {
+      st_release(&status[0], status_word(epoch, kFlagInc, agg));
+    } else {
+      st_release(&status[tile], status_word(epoch, kFlagAgg, agg));
+      int j = (int)tile - 1;
+      while (j >= 0) {
+        uint64_t w;
+        int it = 0;
+        for (;;) {
+          w = ld_acquire(&status[j]);
+          if ((uint32_t)(w >> 34) == epoch && ((w >> 32) & 3u) != 0) break;
+          if (++it > kSpinLimit) {
+            atomicOr(&hdr->err, SET_DEVERR_WAIT);
+            w = status_word(epoch, kFlagInc, 0.f);
+            break;
+          }
+          __nanosleep(32);
+        }
+        prefix += __uint_as_float((uint32_t)w);
+        if (((w >> 32) & 3u) == kFlagInc) break;
+        --j;
+      }
+      st_release(&status[tile], status_word(epoch, kFlagInc, prefix + agg));
+    }
+    s_prefix = prefix;
+  }
+  __syncthreads();
+
+  // S = tile prefix + warp offset + lane offset + thread-serial offset; track max |S|
+  const float off = s_prefix + s_wexcl[warp] + lane_excl;
+  float mx = 0.f;
+  if (vec) {
+#pragma unroll
+    for (int q = 0; q < kPer / 4; ++q) {
+      const float4 s = make_float4(off + e[4 * q], off + e[4 * q + 1], off + e[4 * q + 2], off + e[4 * q + 3]);
+      reinterpret_cast<float4*>(p.S + base)[q] = s;
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(s.x), fabsf(s.y)), fmaxf(fabsf(s.z), fabsf(s.w))));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const size_t i = base + k;
+      if (i < n) {
+        const float s = off + e[k];
+        p.S[i] = s;
+        mx = fmaxf(mx, fabsf(s));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  if (lane == 0) s_wmax[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = s_wmax[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) t = fmaxf(t, s_wmax[w]);
+    tmax[tile] = t;
+    __threadfence();
+    s_last = atomicAdd(&hdr->done, 1u) == p.T - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+
+  // last tile: reduce the per-tile maxima, write m and the trailer, reset the scratch
+  __threadfence();
+  if (warp == 0) {
+    float m = 0.f;
+    for (uint32_t t = lane; t < p.T; t += 32) m = fmaxf(m, *reinterpret_cast<volatile float*>(&tmax[t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if (lane == 0) {
+      p.m_out[0] = m;
+      p.m_out[1] = 0.f;
+      p.m_out[2] = 0.f;
+      p.m_out[3] = 0.f;
+      const uint32_t err = *reinterpret_cast<volatile uint32_t*>(&hdr->err);
+      p.trailer->job_id = p.job_id;
+      p.trailer->slot_gen = p.slot_gen;
+      p.trailer->word = trailer_word(err);
+      hdr->err = 0u;
+      hdr->ticket = 0u;
+      hdr->done = 0u;
+      __threadfence();
+      hdr->epoch = (epoch + 1u) & 0x3FFFFFFFu;
+    }
+  }
+}
+
+inline uint32_t num_tiles(uint32_t n) { return (n + kTile - 1) / kTile; }
+
+}  // namespace
+
+bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk) {
+  const uint32_t n = in.dims[0];
+  ScanArgs a{};
+  a.x = static_cast<const float*>(in.d_in);
+  a.y = a.x + n;
+  a.z = static_cast<float*>(in.d_out);
+  a.S = a.z + n;
+  a.m_out = a.S + n;
+  a.trailer = reinterpret_cast<set_trailer*>(static_cast<uint8_t*>(in.d_out) + L.out_bytes - sizeof(set_trailer));
+  a.scratch = static_cast<uint8_t*>(in.d_persist);
+  a.job_id = in.job_id;
+  a.n = n;
+  a.T = num_tiles(n);
+  a.a = in.scalar;
+  a.slot_gen = in.slot_gen;
+  KernelLaunch& k = kl[0];
+  k.func = reinterpret_cast<const void*>(&saxpy_scan_max_kernel);
+  k.grid = dim3(a.T);
+  k.block = dim3(kThreads);
+  k.smem = 0;
+  k.deps = 0;
+  set_args(k, a);
+  *nk = 1;
+  return true;
+}
+
+}  // namespace setk

@@ -1,0 +1,119 @@
+// executor.h -- the SET executor's host runtime (Sec. 4.2, Algorithms 1-3), independent of how a
+// job reaches the GPU.  The Device interface owns streams, slot memory and graph execs; the
+// Executor owns queues, the free-slot pool, dispatch threads, counters and the completion path.
+#pragma once
+
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "set.h"
+#include "sync.h"
+
+namespace setrt {
+
+class Executor;
+
+struct JobRec {
+  set_job_desc d{};
+  uint64_t id = 0;
+  uint64_t t_submit_ns = 0;
+  uint32_t queued_lane = 0;
+};
+
+// One ring entry of a lane: a device buffer with one graph exec per job type bound to it.
+struct Slot {
+  uint32_t index = 0, lane = 0, ring = 0;
+  uint8_t* dev = nullptr;
+  size_t bytes = 0;
+  uint32_t gen = 0;       // bumped by every completion of this slot
+  JobRec job{};           // job in flight
+  Executor* ex = nullptr;
+  void* dev_state = nullptr;  // owned by the Device
+};
+
+struct LaunchCost {
+  uint64_t updates = 0;   // node parameter updates issued
+  uint64_t update_ns = 0; // host time spent updating
+  uint64_t launch_ns = 0; // host time spent launching and chaining the callback
+};
+
+class Device {
+ public:
+  virtual ~Device() = default;
+  // Allocates slot memory and per-slot graph execs; fills dev / bytes / dev_state of every slot.
+  virtual set_status init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) = 0;
+  // UpdateGraphParams(job, slot) + GraphLaunch on the slot's lane + AddCallback: the callback,
+  // run after the job's D2H copy, must call Executor::on_complete(slot, device_status).
+  virtual set_status launch(Slot& s, LaunchCost* cost, std::string* err) = 0;
+  // Waits for all device work of the context (used at destruction).
+  virtual void drain() = 0;
+  // True if graphs for jobs of this type were instantiated.
+  virtual bool supports(uint32_t type) const = 0;
+  // Runs a baseline programming model over the same slots (the context's workers are idle).
+  virtual set_status run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots,
+                                  LogHist* lat, LaunchCost* cost, uint64_t* t0_ns, uint64_t* t1_ns,
+                                  std::string* err) = 0;
+};
+
+// Product CUDA device; the host-simulation test library links its own factory instead.
+std::unique_ptr<Device> make_device(const set_config& cfg);
+
+class Executor {
+ public:
+  static set_status create(const set_config& cfg, Executor** out, std::string* err);
+  ~Executor();
+
+  set_status submit(const set_job_desc* d, uint64_t* id);                                    // Alg. 1
+  set_status submit_many(const set_job_desc* d, size_t n, uint64_t* first_id, size_t* n_done);
+  set_status wait_all(int64_t timeout_us);
+  void stats(set_stats_t* s) const;
+  void reset_stats();
+  set_status run_baseline(int kind, const set_job_desc* jobs, size_t n, set_stats_t* out);
+  const char* last_error();
+
+  // Algorithm 3 (asynchronous resource return).  Runs on the device's callback thread after the
+  // slot's D2H copy completed: checks the returned trailer, counts the job done, returns the slot
+  // to W_pool and wakes one dispatcher.
+  void on_complete(Slot& s, int32_t dev_status);
+
+  const set_config& config() const { return cfg_; }
+
+ private:
+  explicit Executor(const set_config& cfg);
+  void worker_main(int w);
+  bool find_job(uint32_t lane, JobRec& j, bool& stolen);  // Alg. 2 FindJob
+  set_status validate(const set_job_desc& d, std::string* why) const;
+  set_status fail(set_status st, const std::string& msg);
+  int32_t check_trailer(const Slot& s) const;
+
+  set_config cfg_;
+  std::unique_ptr<Device> dev_;
+  std::vector<Slot> slots_;
+  std::vector<std::unique_ptr<MpmcRing<JobRec>>> queues_;  // Q_i, one per lane
+  std::unique_ptr<MpmcRing<uint32_t>> free_;                // W_pool of slot indices
+  std::vector<std::thread> workers_;
+
+  Signal free_sig_, job_sig_, space_sig_, done_sig_;
+  std::atomic<bool> stop_{false};
+  std::atomic<int> sticky_{SET_OK};
+
+  std::atomic<uint64_t> c_next_{0};       // next job id
+  std::atomic<uint64_t> c_submitted_{0};
+  std::atomic<uint64_t> c_done_{0};
+  std::atomic<uint64_t> c_failed_{0};
+  std::atomic<uint64_t> done_target_{~0ull};
+  std::atomic<uint64_t> steals_{0}, updates_{0}, canary_errors_{0};
+  std::atomic<uint64_t> update_ns_{0}, launch_ns_{0}, launched_{0};
+  std::atomic<uint64_t> t_first_ns_{0}, t_last_ns_{0};
+  std::atomic<uint64_t> stat_base_submitted_{0}, stat_base_done_{0}, stat_base_failed_{0};
+  LogHist lat_;
+
+  std::mutex err_mu_;
+  std::string err_;
+  std::string err_copy_;
+};
+
+}  // namespace setrt

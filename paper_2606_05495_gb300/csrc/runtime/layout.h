@@ -1,0 +1,31 @@
+// layout.h -- byte sizes and slot placement of every job type (host only, no CUDA headers).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace setk {
+
+// A job occupies a slot as [control | in | out | scratch]:
+//   control: persistent state a kernel keeps across launches (zeroed once when the slot is
+//            created, never written by copies or by other job types, always at slot offset 0);
+//   in/out : the H2D and D2H payloads; scratch: transient work buffers of this job.
+// Each region starts on a 256-byte boundary.
+struct JobLayout {
+  size_t in_bytes = 0, out_bytes = 0, scratch_bytes = 0, persist_bytes = 0;
+  size_t in_off = 0, out_off = 0, scratch_off = 0, end = 0;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Sizes of one job; false if type or dims are invalid.
+bool job_sizes(uint32_t type, const uint32_t dims[4], JobLayout* L);
+
+// Control-block bytes reserved at the start of every slot of `slot_bytes`: enough for the
+// persistent state of any job whose payload fits the slot.
+size_t slot_control_bytes(size_t slot_bytes);
+
+// Places the job's regions after a control block of `ctl` bytes.
+void place_job(JobLayout* L, size_t ctl);
+
+}  // namespace setk

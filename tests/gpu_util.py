@@ -1,0 +1,117 @@
+"""Helpers shared by the GPU tests: pinned buffers, job building, running jobs through the executor."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+import datagen
+
+
+def S():
+    import paper_2606_05495_gb300 as mod
+    return mod
+
+
+def torch():
+    import torch as t
+    return t
+
+
+class Job:
+    """One job with its pinned input/output buffers (kept alive until checked)."""
+
+    def __init__(self, type_, dims, payload: np.ndarray, scalar=0.0, shared=(None, None), device=False):
+        s, t = S(), torch()
+        self.type, self.dims, self.scalar, self.payload = type_, tuple(dims), scalar, payload
+        raw = np.ascontiguousarray(payload).view(np.uint8).ravel()
+        ob = s.set_job_out_bytes(type_, s.dims4(*dims))
+        assert raw.size == s.set_job_in_bytes(type_, s.dims4(*dims)) and ob > 0
+        if device:
+            self.hin = t.from_numpy(raw.copy()).cuda()
+            self.hout = t.zeros(ob, dtype=t.uint8, device="cuda")
+        else:
+            self.hin = t.from_numpy(raw.copy()).pin_memory()
+            self.hout = t.full((ob,), 0xAB, dtype=t.uint8).pin_memory()
+        self.status = ctypes.c_int32(99)
+        self.desc = s.make_desc(type_, dims, self.hin.data_ptr(), self.hout.data_ptr(), scalar=scalar,
+                                shared=shared, status=ctypes.pointer(self.status))
+        self.id = None
+
+    def out(self) -> np.ndarray:
+        return self.hout.cpu().numpy() if self.hout.is_cuda else self.hout.numpy()
+
+    def trailer(self):
+        o = self.out()
+        t = o[-16:]
+        return int(t[:8].view(np.uint64)[0]), int(t[8:12].view(np.uint32)[0]), int(t[12:16].view(np.uint32)[0])
+
+
+def run_jobs(jobs, timeout_s=120, **cfg):
+    """Submits every job (set_submit_many), waits, returns the context's stats dict."""
+    s = S()
+    ctx = s.create(s.default_config(**cfg))
+    try:
+        arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+        first = ctypes.c_uint64()
+        s.check(s.set_submit_many(ctx, arr, len(jobs), ctypes.byref(first), None), "set_submit_many", ctx)
+        s.check(s.set_wait_all(ctx, int(timeout_s * 1e6)), "set_wait_all", ctx)
+        for k, j in enumerate(jobs):
+            j.id = first.value + k
+        st = s.set_stats_t()
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "set_stats", ctx)
+        return st.as_dict()
+    finally:
+        s.set_destroy(ctx)
+
+
+def check_trailers(jobs, io_host=True):
+    s = S()
+    for j in jobs:
+        jid, gen, word = j.trailer()
+        assert jid == j.id, (jid, j.id)
+        assert word == (s.SET_TRAILER_MAGIC << 16), hex(word)
+        if io_host:
+            assert j.status.value == s.SET_OK, j.status.value
+
+
+# ---- per-type oracle comparisons ----
+
+def blur_job(j, W=256, H=256, **kw):
+    img = datagen.blur_job(j) if (W, H) == (256, 256) else np.random.default_rng(j).integers(
+        0, 256, (H, W), dtype=np.uint8)
+    return Job(S().SET_JOB_BLUR_HIST, (W, H), img, **kw)
+
+
+def check_blur(job):
+    import oracle
+    W, H = job.dims
+    b, h = oracle.job_blur_hist(job.payload.reshape(H, W))
+    o = job.out()
+    n = W * H
+    off = (n + 15) & ~15
+    assert np.array_equal(o[:n].reshape(H, W), b), f"blurred image mismatch at {W}x{H}"
+    assert not o[n:off].any(), "pad bytes not zero"
+    assert np.array_equal(o[off:off + 1024].view(np.uint32), h), f"histogram mismatch at {W}x{H}"
+
+
+def scan_job(j, n=datagen.SCAN_N, **kw):
+    a, xy = datagen.scan_job(j, n=n)
+    return Job(S().SET_JOB_SAXPY_SCAN_MAX, (n,), xy, scalar=a, **kw)
+
+
+SCAN_RTOL = 1e-5  # |S_gpu - S| <= 1e-5 * sum_{j<i} |z_j|  (fp32 vs the fp64 oracle)
+
+
+def check_scan(job):
+    import oracle
+    n = job.dims[0]
+    xy = job.payload
+    z, Sref, A, m = oracle.job_saxpy_scan_max(job.scalar, xy[:n], xy[n:])
+    f = job.out()[:8 * n + 16].view(np.float32)
+    assert np.array_equal(f[:n], z), "z is not bit-exact"
+    err = np.abs(f[n:2 * n].astype(np.float64) - Sref)
+    assert np.all(err <= SCAN_RTOL * A), f"scan error {np.max(err / np.maximum(A, 1e-300))} x A"
+    assert f[n] == 0.0 if n else True  # S_0 is exactly 0
+    assert abs(float(f[2 * n]) - m) <= SCAN_RTOL * float(A.max()), (float(f[2 * n]), m)
+    assert not f[2 * n + 1:2 * n + 4].any(), "pad after m not zero"

@@ -1,0 +1,93 @@
+"""The C ABI on CPU: libset.so loads, exports every function include/set.h declares, the Python
+structs match the C layouts, and the documented payload sizes hold.  No compute calls."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_2606_05495_gb300 as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "set.h")
+
+
+def declared_functions():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(set_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_function_is_exported():
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(S.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    nm = subprocess.run(["nm", "-D", "--defined-only", S.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (set_\w+)", nm))
+    assert set(names) <= exported
+
+
+STRUCTS = {
+    "set_job_desc": S.set_job_desc,
+    "set_config": S.set_config,
+    "set_stats_t": S.set_stats_t,
+    "set_trailer": S.set_trailer,
+}
+
+
+def test_struct_layouts_match_binding():
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "set.h"', "int main(void){"]
+    for cname, py in STRUCTS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            cf = "in" if fname == "in_" else fname
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {cf}));')
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = STRUCTS[cname]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (cname, field, got, val)
+
+
+def test_documented_payload_sizes():
+    d = S.dims4
+    assert S.set_job_in_bytes(1, d(256, 256)) == 65536
+    assert S.set_job_out_bytes(1, d(256, 256)) == 65536 + 1024 + 16
+    assert S.set_job_out_bytes(1, d(17, 3)) == 64 + 1024 + 16  # 51 bytes padded to 64
+    assert S.set_job_in_bytes(2, d(65536)) == 524288
+    assert S.set_job_out_bytes(2, d(65536)) == 524288 + 32
+    assert S.set_job_in_bytes(3, d(640, 480)) == 640 * 480 * 3
+    assert S.set_job_out_bytes(3, d(641, 3)) == 1936 + 1024 + 16
+    assert S.set_job_in_bytes(4, d(7)) == 7 * 1024 * 2
+    assert S.set_job_out_bytes(4, d(7)) == 7 * 1024 * 4 + 16
+    for t, dims in [(1, d(0, 5)), (1, d(2049, 5)), (2, d(0)), (2, d(1 << 27)), (3, d(4097, 2)), (4, d(0)),
+                    (4, d(257)), (9, d(1, 1))]:
+        assert S.set_job_in_bytes(t, dims) == 0 and S.set_job_out_bytes(t, dims) == 0
+    assert S.set_job_scratch_bytes(2, d(65536)) == 256  # 64-byte header + 16 tiles x 12 bytes, aligned
+    sb = S.set_job_slot_bytes(2, d(65536))
+    assert sb >= 2 * 524288 and sb < 2 * 524288 + 4096
+
+
+def test_config_defaults():
+    c = S.default_config()
+    assert (c.num_streams, c.num_workers, c.ring_depth, c.queue_capacity, c.steal) == (2, 2, 2, 4, 1)
+    assert c.io_mode == S.SET_IO_HOST and c.img_fused == 1 and c.drain_timeout_ms == 30000
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = ctypes.c_void_p()
+    assert S.set_create(2, 2, 1 << 20, ctypes.byref(ctx)) == S.SET_ECUDA
+    assert S.set_last_error(None)
+    assert S.set_submit(None, None, None) == S.SET_EINVAL

@@ -1,0 +1,100 @@
+"""GPU parity of the blur and scan jobs through the C ABI (executor and direct launches)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_util import S, blur_job, check_blur, check_scan, check_trailers, run_jobs, scan_job, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_blur_config_64_jobs_2_streams():
+    jobs = [blur_job(j) for j in range(64)]
+    st = run_jobs(jobs, num_streams=2, num_workers=2, slot_bytes=1 << 20)
+    assert st["completed"] == 64 and st["failed"] == 0 and st["canary_errors"] == 0
+    for j in jobs:
+        check_blur(j)
+    check_trailers(jobs)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (16, 16), (17, 3), (33, 7), (300, 9), (255, 257),
+                                 (2048, 40), (64, 1000)])
+def test_blur_edge_sizes(W, H):
+    jobs = [blur_job(k, W=W, H=H) for k in range(3)]
+    st = run_jobs(jobs, num_streams=2, num_workers=1, slot_bytes=4 << 20)
+    assert st["failed"] == 0
+    for j in jobs:
+        check_blur(j)
+    check_trailers(jobs)
+
+
+def test_scan_config_4096_jobs_8_streams_stealing():
+    jobs = [scan_job(j) for j in range(4096)]
+    st = run_jobs(jobs, timeout_s=300, num_streams=8, num_workers=8, ring_depth=2,
+                  slot_bytes=S().set_job_slot_bytes(2, S().dims4(65536)))
+    assert st["completed"] == 4096 and st["failed"] == 0 and st["canary_errors"] == 0
+    for j in jobs:
+        check_scan(j)
+    check_trailers(jobs)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 4095, 4096, 4097, 65537, 100003, 1 << 20])
+def test_scan_edge_sizes(n):
+    jobs = [scan_job(k, n=n) for k in range(3)]
+    st = run_jobs(jobs, num_streams=2, num_workers=2, slot_bytes=max(1 << 20, 20 * n + 65536))
+    assert st["failed"] == 0
+    for j in jobs:
+        check_scan(j)
+    check_trailers(jobs)
+
+
+def test_mixed_types_share_slots_without_stealing():
+    jobs = []
+    for k in range(40):
+        jobs.append(blur_job(k) if k % 2 else scan_job(k, n=65536 - 7 * k))
+    st = run_jobs(jobs, num_streams=3, num_workers=2, slot_bytes=2 << 20, steal=0)
+    assert st["failed"] == 0 and st["steals"] == 0
+    for j in jobs:
+        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+    check_trailers(jobs)
+
+
+def test_device_io_mode():
+    jobs = [scan_job(k, device=True) for k in range(16)] + [blur_job(k, device=True) for k in range(16)]
+    st = run_jobs(jobs, num_streams=4, num_workers=2, slot_bytes=2 << 20, io_mode=S().SET_IO_DEVICE)
+    assert st["failed"] == 0 and st["completed"] == 32
+    for j in jobs:
+        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+    check_trailers(jobs, io_host=False)
+
+
+def test_direct_launch_reuses_scan_scratch_across_sizes():
+    s, t = S(), torch()
+    ns = [65536, 1, 4097, 300000, 4096, 7]
+    scratch = t.zeros(max(s.set_job_scratch_bytes(2, s.dims4(n)) for n in ns), dtype=t.uint8, device="cuda")
+    stream = t.cuda.current_stream().cuda_stream
+    for k, n in enumerate(ns):
+        j = scan_job(k, n=n, device=True)
+        st = s.set_launch_job(ctypes.byref(j.desc), j.hin.data_ptr(), j.hout.data_ptr(), scratch.data_ptr(), 1000 + k, 0,
+                              stream)
+        assert st == 0
+        t.cuda.synchronize()
+        check_scan(j)
+        assert j.trailer()[0] == 1000 + k
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_baselines_compute_the_same_results(kind):
+    s = S()
+    jobs = [scan_job(k) for k in range(10)] + [blur_job(k) for k in range(10)]
+    ctx = s.create(s.default_config(num_streams=4, num_workers=2, slot_bytes=2 << 20))
+    try:
+        arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+        st = s.set_stats_t()
+        s.check(s.set_run_baseline(ctx, kind, arr, len(jobs), ctypes.byref(st)), "set_run_baseline", ctx)
+        assert st.completed == len(jobs) and st.jobs_per_s > 0
+    finally:
+        s.set_destroy(ctx)
+    for j in jobs:
+        (check_blur if j.type == s.SET_JOB_BLUR_HIST else check_scan)(j)
