@@ -261,33 +261,15 @@ def timed(S, ctx, descs, n, args, d: Dist):
     return d.max(ms), st.as_dict()
 
 
-def copy_rates(device_index: int, job_bytes: int, streams: int, reps: int = 1024):
-    """Pinned copy rates (GB/s) at the job's own size, `streams` streams back to back:
-    H2D alone, D2H alone, and H2D + D2H together (total bytes both ways)."""
-    t = _torch()
-    dev = f"cuda:{device_index}"
-    hs = [t.empty(job_bytes, dtype=t.uint8, pin_memory=True) for _ in range(streams)]
-    ho = [t.empty(job_bytes, dtype=t.uint8, pin_memory=True) for _ in range(streams)]
-    ds = [t.empty(job_bytes, dtype=t.uint8, device=dev) for _ in range(streams)]
-    do = [t.empty(job_bytes, dtype=t.uint8, device=dev) for _ in range(streams)]
-    ss = [t.cuda.Stream() for _ in range(streams)]
-
-    def go(h2d: bool, d2h: bool):
-        t.cuda.synchronize()
-        t0 = time.perf_counter()
-        for r in range(reps):
-            i = r % streams
-            with t.cuda.stream(ss[i]):
-                if h2d:
-                    ds[i].copy_(hs[i], non_blocking=True)
-                if d2h:
-                    ho[i].copy_(do[i], non_blocking=True)
-        t.cuda.synchronize()
-        return time.perf_counter() - t0
-
-    go(True, True)
-    b = reps * job_bytes / 1e9
-    return {"h2d_gbs": b / go(True, False), "d2h_gbs": b / go(False, True), "bidir_total_gbs": 2 * b / go(True, True)}
+def copy_rates(S, job_in: int, job_out: int, streams: int, reps: int = 2048):
+    """Pinned copy rates (GB/s) at the job's own sizes, `streams` streams back to back, timed in C
+    (set_copy_bandwidth): H2D alone, D2H alone, and H2D + D2H together (total bytes both ways)."""
+    out = {}
+    for name, nbytes, direction in (("h2d_gbs", job_in, 0), ("d2h_gbs", job_out, 1), ("bidir_total_gbs", job_in, 2)):
+        g = ctypes.c_double()
+        S.check(S.set_copy_bandwidth(nbytes, streams, reps, direction, ctypes.byref(g)), "set_copy_bandwidth")
+        out[name] = g.value
+    return out
 
 
 def kernel_time(S, w: Workload, launches: int = 512):
@@ -349,7 +331,7 @@ def run_set(args, d: Dist):
     S.set_destroy(ctx)
 
     k_mean_us, k_med_us = kernel_time(S, w)
-    rates = copy_rates(dev_index, JOB_IN, args.streams)
+    rates = copy_rates(S, JOB_IN, JOB_OUT, args.streams)
     world = d.world
     value = world * nj / (ms_dev * 1e-3)
     e2e = world * nj / (ms_host * 1e-3)

@@ -130,6 +130,11 @@ typedef struct {
   uint32_t type_mask;  /* bit (1 << type) per job type to instantiate graphs for; 0 = all */
   int device;          /* CUDA device ordinal (default 0) */
   int drain_timeout_ms; /* set_destroy waits at most this long for jobs in flight (default 30000) */
+  int cb_mode;         /* 0 (default): completion callback on a per-lane callback stream that waits
+                          on an event recorded behind the graph (the lane never waits on the host);
+                          1: cudaLaunchHostFunc directly on the lane stream */
+  int spin_us;         /* dispatch workers spin this long on an empty pool / queue before they
+                          sleep on a futex (default 50; 0 = sleep at once) */
 } set_config;
 
 typedef struct {
@@ -206,6 +211,14 @@ set_status set_launch_job(const set_job_desc* job, const void* d_in, void* d_out
 
 /* Number of kernels set_launch_job launches for this job (graph kernel nodes per job). */
 int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused);
+
+/* ---- measurement helpers ---- */
+
+/* Pinned-host <-> device copy bandwidth in GB/s for copies of `bytes` issued back to back,
+ * round-robin over `streams` streams, `reps` copies in all.  dir 0 = H2D, 1 = D2H, 2 = H2D and
+ * D2H together (bytes counted both ways).  Allocates and frees its own buffers on the current
+ * device.  Used for the pipeline bound of the measured throughput. */
+set_status set_copy_bandwidth(size_t bytes, int streams, int reps, int dir, double* gbs);
 
 /* ---- baselines run on the same kernels (Sec. 5.1.3) ---- */
 

@@ -45,7 +45,7 @@ class set_config(ctypes.Structure):
     _fields_ = [("num_streams", c_int), ("num_workers", c_int), ("slot_bytes", c_size_t), ("ring_depth", c_int),
                 ("queue_capacity", c_int), ("steal", c_int), ("io_mode", c_int), ("img_fused", c_int),
                 ("pool", c_void_p), ("pool_bytes", c_size_t), ("type_mask", c_uint32), ("device", c_int),
-                ("drain_timeout_ms", c_int)]
+                ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int)]
 
 
 class set_stats_t(ctypes.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "set_launch_job": ([POINTER(set_job_desc), c_void_p, c_void_p, c_void_p, c_uint64, c_uint32, c_void_p], c_int),
     "set_job_kernel_count": ([c_uint32, _dims, c_int], c_int),
     "set_run_baseline": ([c_void_p, c_int, POINTER(set_job_desc), c_size_t, POINTER(set_stats_t)], c_int),
+    "set_copy_bandwidth": ([c_size_t, c_int, c_int, c_int, POINTER(c_double)], c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)

@@ -1,0 +1,402 @@
+// img_sobel_hist.cu -- image job: gray = (77R + 150G + 29B) >> 8, 5x5 Gaussian [1,4,6,4,1] (x)
+// [1,4,6,4,1] >> 8, Sobel min(|gx| + |gy|, 255), 256-bin histogram of the Sobel image.  Every
+// stage clamps its own input at the border (replicate edge).
+//
+// Two forms over the same device functions:
+//   - per stage: gray_kernel, gauss_kernel, sobel_hist_kernel (three graph nodes in a chain);
+//   - fused: img_fused_kernel computes RGB -> Sobel + histogram per tile with a 3-pixel halo, and
+//     takes a table of jobs, so one persistent launch can carry many uneven images (the batched
+//     form).  CTAs pull work items (a band of up to 32 rows x 512 columns of one job) from an
+//     atomic ticket, stage tiles of 32 x 128 output pixels in shared memory and never write the
+//     gray or Gaussian images to global memory.
+//
+// Clamping in the fused halo: the Sobel stencil needs the Gaussian *of the border pixel* at
+// out-of-image positions (q[cl(y)][cl(x)]), not a Gaussian evaluated at an outside coordinate.
+// The Gaussian tile is therefore evaluated at the clamped centre of every halo position; the gray
+// tile holds g[cl(Y)][cl(X)] for every staged coordinate, so clamp(centre) + offset reproduces the
+// per-stage definition exactly.
+//
+// Histogram: per-warp privatised shared histograms; at the end of a work item the CTA adds its
+// non-zero bins into the job's accumulator (persistent per-job state, zero at kernel start); the
+// CTA that completes the job's last item (items-done counter) copies the accumulator into the
+// job's output, zeroes it and resets the counter, then writes the pad and the trailer.  The last
+// CTA to leave resets the ticket.  No zeroing pass, no memset node.
+#include "stages.h"
+
+namespace setk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRB = 32;   // output rows of a tile (= band rows)
+constexpr int kTW = 128;  // output columns of a tile
+static_assert(kRB == kImgBandRows, "band rows shared with the layout code");
+static_assert(kImgChunkCols % kTW == 0, "a work item is a whole number of tiles wide");
+
+struct ImgJobDev {
+  const uint8_t* rgb;
+  uint8_t* out;         // Sobel image, W*H bytes
+  uint8_t* pad;         // zero bytes up to the histogram
+  uint32_t* hist;       // 256 u32
+  set_trailer* trailer;
+  uint32_t* acc;        // persistent [256] accumulator, acc[256] = items done
+  uint64_t job_id;
+  uint32_t W, H;
+  uint32_t item0, nitems;  // first global work item of this job, number of items
+  uint32_t chunks;         // column chunks per band
+  uint32_t slot_gen, npad;
+  uint32_t pad_;
+};
+
+struct ImgHdr {
+  uint32_t ticket;
+  uint32_t pad[15];
+};
+static_assert(sizeof(ImgHdr) == kImgHdrBytes, "image header size shared with the layout code");
+
+struct ImgFusedArgs {
+  const ImgJobDev* table;  // device table of njobs entries, or nullptr: use `one`
+  ImgHdr* hdr;
+  uint32_t njobs, total_items;
+  ImgJobDev one;
+};
+
+struct SobelHistArgs {
+  ImgFusedArgs a;
+  const uint8_t* q;  // Gaussian image
+};
+
+struct GrayArgs {
+  const uint8_t* rgb;
+  uint8_t* gray;
+  size_t px;
+};
+
+struct GaussArgs {
+  const uint8_t* g;
+  uint8_t* q;
+  uint32_t W, H;
+};
+
+__device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
+
+__device__ __forceinline__ uint32_t gray_of(uint32_t r, uint32_t g, uint32_t b) { return (77u * r + 150u * g + 29u * b) >> 8; }
+
+// g_s[r][c] = gray(rgb[cl(y0 + r)][cl(x0 + c)]) for r < GR, c < GC.
+template <int GR, int GC, int P>
+__device__ void stage_gray(uint8_t (*g_s)[P], const uint8_t* __restrict__ rgb, int W, int H, int y0, int x0) {
+  for (int i = threadIdx.x; i < GR * GC; i += kThreads) {
+    const int r = i / GC, c = i - r * GC;
+    const uint8_t* p = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + clampi(x0 + c, W));
+    g_s[r][c] = (uint8_t)gray_of(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+  }
+}
+
+// s_s[r][c] = img[cl(y0 + r)][cl(x0 + c)] for r < R, c < C.
+template <int R, int C, int P>
+__device__ void stage_u8(uint8_t (*s_s)[P], const uint8_t* __restrict__ img, int W, int H, int y0, int x0) {
+  for (int i = threadIdx.x; i < R * C; i += kThreads) {
+    const int r = i / C, c = i - r * C;
+    s_s[r][c] = __ldg(img + (size_t)clampi(y0 + r, H) * W + clampi(x0 + c, W));
+  }
+}
+
+// Gaussian of the QR x QC positions starting at (qy0, qx0), each evaluated at its clamped centre:
+// q_s[r][c] = (sum_ij w_i w_j g[cl(cl(qy0+r)+i)][cl(cl(qx0+c)+j)]) >> 8, where g_s[r][c] holds
+// g[cl(gy0 + r)][cl(gx0 + c)].  Separable in exact integer arithmetic (vertical then horizontal).
+template <int QR, int QC, int GC, int GP, int VP, int QP>
+__device__ void gauss_tile(uint8_t (*q_s)[QP], const uint8_t (*g_s)[GP], uint16_t (*v_s)[VP], int W, int H, int qy0,
+                           int qx0, int gy0, int gx0) {
+  for (int i = threadIdx.x; i < QR * GC; i += kThreads) {
+    const int r = i / GC, c = i - r * GC;
+    const int cy = clampi(qy0 + r, H) - gy0;
+    const uint32_t v = (uint32_t)g_s[cy - 2][c] + 4u * g_s[cy - 1][c] + 6u * g_s[cy][c] + 4u * g_s[cy + 1][c] +
+                       (uint32_t)g_s[cy + 2][c];
+    v_s[r][c] = (uint16_t)v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < QR * QC; i += kThreads) {
+    const int r = i / QC, c = i - r * QC;
+    const int cx = clampi(qx0 + c, W) - gx0;
+    const uint32_t s = (uint32_t)v_s[r][cx - 2] + 4u * v_s[r][cx - 1] + 6u * v_s[r][cx] + 4u * v_s[r][cx + 1] +
+                       (uint32_t)v_s[r][cx + 2];
+    q_s[r][c] = (uint8_t)(s >> 8);
+  }
+}
+
+// Sobel of the tile's output pixels: thread t computes 16 pixels of row t/8.  q_s[r][c] holds
+// q[cl(y0 - 1 + r)][cl(x0 - 1 + c)].  Writes the pixels inside the image and counts them.
+template <int QP>
+__device__ void sobel_tile(const uint8_t (*q_s)[QP], uint8_t* __restrict__ out, uint32_t (*whist)[256], int W, int H,
+                           int y0, int x0, bool vec) {
+  const int r = threadIdx.x >> 3, s = (threadIdx.x & 7) << 4;
+  const int y = y0 + r;
+  if (y >= H || x0 + s >= W) return;
+  const uint8_t* a = q_s[r] + s;  // row y-1, columns x-1 ..
+  const uint8_t* b = q_s[r + 1] + s;
+  const uint8_t* c = q_s[r + 2] + s;
+  uint32_t o[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int gx = ((int)a[k + 2] + 2 * b[k + 2] + c[k + 2]) - ((int)a[k] + 2 * b[k] + c[k]);
+    const int gy = ((int)c[k] + 2 * c[k + 1] + c[k + 2]) - ((int)a[k] + 2 * a[k + 1] + a[k + 2]);
+    const uint32_t m = (uint32_t)min(abs(gx) + abs(gy), 255);
+    o[k >> 2] |= m << (8 * (k & 3));
+  }
+  uint8_t* dst = out + (size_t)y * W + x0 + s;
+  const int nvalid = min(16, W - (x0 + s));
+  uint32_t(*h)[256] = whist;
+  const int w = threadIdx.x >> 5;
+  if (vec && nvalid == 16) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+  } else {
+    for (int k = 0; k < nvalid; ++k) dst[k] = (uint8_t)(o[k >> 2] >> (8 * (k & 3)));
+  }
+  for (int k = 0; k < nvalid; ++k) atomicAdd(&h[w][(o[k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+}
+
+__device__ __forceinline__ const ImgJobDev& find_job(const ImgFusedArgs& a, uint32_t item) {
+  if (!a.table) return a.one;
+  uint32_t lo = 0, hi = a.njobs - 1;  // last job with item0 <= item
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (a.table[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  return a.table[lo];
+}
+
+// Adds the CTA's histogram into the job accumulator; the CTA finishing the job's last item
+// publishes the histogram, pad and trailer and leaves the accumulator zeroed.
+__device__ void finish_item(const ImgJobDev& j, uint32_t (*whist)[256], uint32_t* s_flag) {
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += kThreads) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      t += whist[w][b];
+      whist[w][b] = 0;
+    }
+    if (t) atomicAdd(&j.acc[b], t);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_flag = atomicAdd(&j.acc[256], 1u) == j.nitems - 1;
+  __syncthreads();
+  if (*s_flag) {
+    __threadfence();
+    for (int b = threadIdx.x; b < 256; b += kThreads) {
+      j.hist[b] = atomicExch(&j.acc[b], 0u);
+    }
+    if (threadIdx.x < (int)j.npad) j.pad[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      j.acc[256] = 0u;
+      j.trailer->job_id = j.job_id;
+      j.trailer->slot_gen = j.slot_gen;
+      j.trailer->word = trailer_word(0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs a) {
+  constexpr int GR = kRB + 6, GC = kTW + 6, QR = kRB + 2, QC = kTW + 2, P = kTW + 8;
+  __shared__ __align__(16) uint8_t g_s[GR][P];
+  __shared__ __align__(16) uint16_t v_s[QR][P];
+  __shared__ __align__(16) uint8_t q_s[QR][P];
+  __shared__ uint32_t whist[kWarps][256];
+  __shared__ uint32_t s_item, s_flag;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&whist[0][0])[i] = 0u;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= a.total_items) {
+      if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;  // last CTA out
+      return;
+    }
+    const ImgJobDev& j = find_job(a, item);
+    const int W = (int)j.W, H = (int)j.H;
+    const uint32_t local = item - j.item0;
+    const int band = (int)(local / j.chunks), chunk = (int)(local - (uint32_t)band * j.chunks);
+    const int y0 = band * kRB;
+    const int xa = chunk * kImgChunkCols, xb = min(W, xa + kImgChunkCols);
+    const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
+    for (int x0 = xa; x0 < xb; x0 += kTW) {
+      stage_gray<GR, GC, P>(g_s, j.rgb, W, H, y0 - 3, x0 - 3);
+      __syncthreads();
+      gauss_tile<QR, QC, GC, P, P, P>(q_s, g_s, v_s, W, H, y0 - 1, x0 - 1, y0 - 3, x0 - 3);
+      __syncthreads();
+      sobel_tile<P>(q_s, j.out, whist, W, H, y0, x0, vec);
+      __syncthreads();
+    }
+    finish_item(j, whist, &s_flag);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) gray_kernel(const GrayArgs a) {
+  const size_t groups = (a.px + 15) / 16;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.rgb) | reinterpret_cast<uintptr_t>(a.gray)) & 15) == 0;
+  for (size_t g = (size_t)blockIdx.x * kThreads + threadIdx.x; g < groups; g += (size_t)gridDim.x * kThreads) {
+    const size_t p0 = g * 16;
+    if (vec && p0 + 16 <= a.px) {
+      uint4 w[3];
+      const uint4* src = reinterpret_cast<const uint4*>(a.rgb + 3 * p0);
+      w[0] = __ldg(src);
+      w[1] = __ldg(src + 1);
+      w[2] = __ldg(src + 2);
+      const uint8_t* b = reinterpret_cast<const uint8_t*>(w);
+      uint32_t o[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[k >> 2] |= gray_of(b[3 * k], b[3 * k + 1], b[3 * k + 2]) << (8 * (k & 3));
+      *reinterpret_cast<uint4*>(a.gray + p0) = make_uint4(o[0], o[1], o[2], o[3]);
+    } else {
+      for (size_t p = p0; p < min(p0 + 16, a.px); ++p)
+        a.gray[p] = (uint8_t)gray_of(a.rgb[3 * p], a.rgb[3 * p + 1], a.rgb[3 * p + 2]);
+    }
+  }
+}
+
+// One CTA per 32 x 128 output tile of the Gaussian image.
+__global__ void __launch_bounds__(kThreads) gauss_kernel(const GaussArgs a) {
+  constexpr int GR = kRB + 4, GC = kTW + 4, P = kTW + 8;
+  __shared__ __align__(16) uint8_t g_s[GR][P];
+  __shared__ __align__(16) uint16_t v_s[kRB][P];
+  __shared__ __align__(16) uint8_t q_s[kRB][P];
+  const int W = (int)a.W, H = (int)a.H;
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kRB;
+  stage_u8<GR, GC, P>(g_s, a.g, W, H, y0 - 2, x0 - 2);
+  __syncthreads();
+  gauss_tile<kRB, kTW, GC, P, P, P>(q_s, g_s, v_s, W, H, y0, x0, y0 - 2, x0 - 2);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRB * kTW; i += kThreads) {
+    const int r = i / kTW, c = i - r * kTW;
+    if (y0 + r < H && x0 + c < W) a.q[(size_t)(y0 + r) * W + x0 + c] = q_s[r][c];
+  }
+}
+
+// Sobel + histogram over the Gaussian image: same work items, tiles and histogram protocol as
+// the fused kernel (single job).
+__global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArgs sa) {
+  const ImgFusedArgs& a = sa.a;
+  const uint8_t* __restrict__ q = sa.q;
+  constexpr int QR = kRB + 2, QC = kTW + 2, P = kTW + 8;
+  __shared__ __align__(16) uint8_t q_s[QR][P];
+  __shared__ uint32_t whist[kWarps][256];
+  __shared__ uint32_t s_item, s_flag;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&whist[0][0])[i] = 0u;
+  const ImgJobDev& j = a.one;
+  const int W = (int)j.W, H = (int)j.H;
+  const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= a.total_items) {
+      if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;
+      return;
+    }
+    const int band = (int)(item / j.chunks), chunk = (int)(item - (uint32_t)band * j.chunks);
+    const int y0 = band * kRB;
+    const int xa = chunk * kImgChunkCols, xb = min(W, xa + kImgChunkCols);
+    for (int x0 = xa; x0 < xb; x0 += kTW) {
+      stage_u8<QR, QC, P>(q_s, q, W, H, y0 - 1, x0 - 1);
+      __syncthreads();
+      sobel_tile<P>(q_s, j.out, whist, W, H, y0, x0, vec);
+      __syncthreads();
+    }
+    finish_item(j, whist, &s_flag);
+  }
+}
+
+uint32_t items_of(uint32_t W, uint32_t H, uint32_t* chunks) {
+  *chunks = (W + kImgChunkCols - 1) / kImgChunkCols;
+  return ((H + kRB - 1) / kRB) * *chunks;
+}
+
+ImgJobDev job_dev(const JobPlanIn& in, const JobLayout& L) {
+  ImgJobDev j{};
+  const uint32_t W = in.dims[0], H = in.dims[1];
+  const size_t px = (size_t)W * H, hist_off = (px + 15) & ~size_t(15);
+  uint8_t* out = static_cast<uint8_t*>(in.d_out);
+  j.rgb = static_cast<const uint8_t*>(in.d_in);
+  j.out = out;
+  j.pad = out + px;
+  j.npad = (uint32_t)(hist_off - px);
+  j.hist = reinterpret_cast<uint32_t*>(out + hist_off);
+  j.trailer = reinterpret_cast<set_trailer*>(out + L.out_bytes - sizeof(set_trailer));
+  j.acc = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(in.d_persist) + kImgHdrBytes);
+  j.job_id = in.job_id;
+  j.W = W;
+  j.H = H;
+  j.item0 = 0;
+  j.nitems = items_of(W, H, &j.chunks);
+  j.slot_gen = in.slot_gen;
+  return j;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+}  // namespace
+
+bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk) {
+  const ImgJobDev j = job_dev(in, L);
+  ImgFusedArgs fa{};
+  fa.table = nullptr;
+  fa.hdr = static_cast<ImgHdr*>(in.d_persist);
+  fa.njobs = 1;
+  fa.total_items = j.nitems;
+  fa.one = j;
+  const uint32_t grid = std::min<uint32_t>(j.nitems, (uint32_t)sm_count() * 4);
+  if (in.img_fused) {
+    KernelLaunch& k = kl[0];
+    k.func = reinterpret_cast<const void*>(&img_fused_kernel);
+    k.grid = dim3(grid);
+    k.block = dim3(kThreads);
+    k.deps = 0;
+    set_args(k, fa);
+    *nk = 1;
+    return true;
+  }
+  const uint32_t W = in.dims[0], H = in.dims[1];
+  const size_t px = (size_t)W * H;
+  uint8_t* gray = static_cast<uint8_t*>(in.d_scratch);
+  uint8_t* gauss = gray + align256(px);
+  GrayArgs ga{j.rgb, gray, px};
+  KernelLaunch& k0 = kl[0];
+  k0.func = reinterpret_cast<const void*>(&gray_kernel);
+  k0.grid = dim3((unsigned)std::min<size_t>((px + 16 * kThreads - 1) / (16 * kThreads), (size_t)sm_count() * 8));
+  k0.block = dim3(kThreads);
+  k0.deps = 0;
+  set_args(k0, ga);
+  GaussArgs qa{gray, gauss, W, H};
+  KernelLaunch& k1 = kl[1];
+  k1.func = reinterpret_cast<const void*>(&gauss_kernel);
+  k1.grid = dim3((W + kTW - 1) / kTW, (H + kRB - 1) / kRB);
+  k1.block = dim3(kThreads);
+  k1.deps = 1u << 0;
+  set_args(k1, qa);
+  SobelHistArgs sa{fa, gauss};
+  KernelLaunch& k2 = kl[2];
+  k2.func = reinterpret_cast<const void*>(&sobel_hist_kernel);
+  k2.grid = dim3(grid);
+  k2.block = dim3(kThreads);
+  k2.deps = 1u << 1;
+  set_args(k2, sa);
+  *nk = 3;
+  return true;
+}
+
+// Batched form: one fused launch over many image jobs (device job table prepared by the caller).
+size_t img_batch_table_bytes(uint32_t njobs) { return sizeof(ImgJobDev) * njobs; }
+
+}  // namespace setk

@@ -14,6 +14,16 @@ constexpr uint32_t kScanHdrBytes = 64;     // {ticket, done, epoch, err} + paddi
 constexpr uint32_t kScanBytesPerTile = 12; // 64-bit status word + float tile max
 
 constexpr int kImgMaxSide = 4096;
+constexpr uint32_t kImgHdrBytes = 64;        // {ticket} + padding
+constexpr uint32_t kImgJobStateBytes = 1152; // hist accumulator [256] u32 + items-done counter, padded
+constexpr int kImgBandRows = 32;             // output rows of one work item
+constexpr int kImgChunkCols = 512;           // output columns of one work item
+constexpr int kImgMaxBatch = 4096;           // jobs of one batched launch
+
+// Slot control block: [image state (fixed) | scan state (grows with the slot)].
+constexpr uint32_t kCtlImgOff = 0;
+constexpr uint32_t kCtlImgBytes = 2048;
+constexpr uint32_t kCtlScanOff = kCtlImgBytes;
 
 constexpr int kMlpD = 1024;
 constexpr int kMlpF = 4096;

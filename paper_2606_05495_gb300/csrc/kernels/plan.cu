@@ -11,6 +11,8 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
       return plan_blur_hist(in, L, kl, nk);
     case SET_JOB_SAXPY_SCAN_MAX:
       return plan_saxpy_scan_max(in, L, kl, nk);
+    case SET_JOB_IMG_SOBEL_HIST:
+      return plan_img_sobel_hist(in, L, kl, nk);
     default:
       return false;
   }

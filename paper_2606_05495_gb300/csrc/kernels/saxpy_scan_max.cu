@@ -4,8 +4,9 @@
 // Tiles of 4096 elements (256 threads x 16 contiguous elements, 16-byte loads and stores).
 // Tiles take a ticket from an atomic counter so that tile ids follow scheduling order, and
 // resolve their prefix with decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
-// Scan with Decoupled Look-back", 2016): each tile publishes its aggregate, then walks back over
-// predecessors' status words until it meets an inclusive prefix.  Inside a tile the scan is
+// Scan with Decoupled Look-back", 2016): each tile publishes its aggregate, then one warp reads
+// the status words of 32 predecessors per round trip and sums back to the nearest inclusive
+// prefix.  Inside a tile the scan is
 // thread-serial, then warp-shuffle, then across the 8 warps.  Each tile also publishes its
 // max|S|; the last tile to finish (done counter) reduces them into m and writes the trailer.
 //
@@ -138,35 +139,52 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   }
   __syncthreads();
 
-  // decoupled look-back across tiles (one thread)
-  if (tid == 0) {
+  // decoupled look-back across tiles, one warp: each round reads the status words of the 32
+  // nearest unresolved predecessors at once, waits until all are published, then sums back to
+  // the nearest inclusive prefix (positions before tile 0 count as an inclusive prefix of 0)
+  if (warp == 0) {
     const float agg = s_agg;
-    float prefix = 0.f;
     if (tile == 0) {
-      st_release(&status[0], status_word(epoch, kFlagInc, agg));
+      if (lane == 0) st_release(&status[0], status_word(epoch, kFlagInc, agg));
+      if (lane == 0) s_prefix = 0.f;
     } else {
-      st_release(&status[tile], status_word(epoch, kFlagAgg, agg));
-      int j = (int)tile - 1;
-      while (j >= 0) {
-        uint64_t w;
-        int it = 0;
-        for (;;) {
-          w = ld_acquire(&status[j]);
-          if ((uint32_t)(w >> 34) == epoch && ((w >> 32) & 3u) != 0) break;
-          if (++it > kSpinLimit) {
-            atomicOr(&hdr->err, SET_DEVERR_WAIT);
-            w = status_word(epoch, kFlagInc, 0.f);
-            break;
+      if (lane == 0) st_release(&status[tile], status_word(epoch, kFlagAgg, agg));
+      float prefix = 0.f;
+      int base = (int)tile - 1;
+      for (;;) {
+        const int j = base - lane;
+        uint32_t flag = kFlagInc;
+        float v = 0.f;
+        if (j >= 0) {
+          int it = 0;
+          uint64_t w;
+          for (;;) {
+            w = ld_acquire(&status[j]);
+            if ((uint32_t)(w >> 34) == epoch && ((w >> 32) & 3u) != 0) break;
+            if (++it > kSpinLimit) {
+              atomicOr(&hdr->err, SET_DEVERR_WAIT);
+              w = status_word(epoch, kFlagInc, 0.f);
+              break;
+            }
+            __nanosleep(20);
           }
-          __nanosleep(32);
+          flag = (uint32_t)(w >> 32) & 3u;
+          v = __uint_as_float((uint32_t)w);
         }
-        prefix += __uint_as_float((uint32_t)w);
-        if (((w >> 32) & 3u) == kFlagInc) break;
-        --j;
+        const unsigned inc = __ballot_sync(0xFFFFFFFFu, flag == kFlagInc);
+        const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive prefix in this window
+        float t = lane <= stop ? v : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        prefix += t;
+        if (inc) break;
+        base -= 32;
       }
-      st_release(&status[tile], status_word(epoch, kFlagInc, prefix + agg));
+      if (lane == 0) {
+        st_release(&status[tile], status_word(epoch, kFlagInc, prefix + agg));
+        s_prefix = prefix;
+      }
     }
-    s_prefix = prefix;
   }
   __syncthreads();
 

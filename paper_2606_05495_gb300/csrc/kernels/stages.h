@@ -50,6 +50,7 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk);
 // Per-type planners (one per kernel source file).
 bool plan_blur_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
+bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 
 // One-time function attributes (dynamic shared memory limits, cluster sizes).
 cudaError_t kernels_init();

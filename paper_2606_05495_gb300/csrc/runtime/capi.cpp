@@ -64,6 +64,8 @@ void set_config_default(set_config* c) {
   c->type_mask = 0;
   c->device = 0;
   c->drain_timeout_ms = 30000;
+  c->cb_mode = 0;
+  c->spin_us = 50;
 }
 
 set_status set_create_ex(const set_config* cfg, set_ctx** out) {

@@ -170,7 +170,7 @@ bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::
   in.d_in = s.dev + L->in_off;
   in.d_out = s.dev + L->out_off;
   in.d_scratch = s.dev + L->scratch_off;
-  in.d_persist = s.dev;
+  in.d_persist = s.dev + setk::control_offset(j.d.type);
   in.job_id = j.id;
   in.slot_gen = s.gen;
   in.img_fused = cfg_.img_fused;
@@ -264,9 +264,13 @@ set_status CudaDevice::launch(Slot& s, LaunchCost* cost, std::string* err) {
   const uint64_t t1 = now_ns();
   cudaStream_t lane = lanes_[s.lane], cb = cbs_[s.lane];
   SET_CK(cudaGraphLaunch(gi.exec, lane));
-  SET_CK(cudaEventRecord(ss.done, lane));
-  SET_CK(cudaStreamWaitEvent(cb, ss.done, 0));
-  SET_CK(cudaLaunchHostFunc(cb, host_complete, &s));
+  if (cfg_.cb_mode == 1) {
+    SET_CK(cudaLaunchHostFunc(lane, host_complete, &s));
+  } else {
+    SET_CK(cudaEventRecord(ss.done, lane));
+    SET_CK(cudaStreamWaitEvent(cb, ss.done, 0));
+    SET_CK(cudaLaunchHostFunc(cb, host_complete, &s));
+  }
   cost->launch_ns += now_ns() - t1;
   return SET_OK;
 }
@@ -403,6 +407,61 @@ extern "C" set_status set_launch_job(const set_job_desc* job, const void* d_in, 
     if (cudaLaunchKernel(kl[k].func, kl[k].grid, kl[k].block, kl[k].params, kl[k].smem, st) != cudaSuccess)
       return SET_ECUDA;
   return SET_OK;
+}
+
+extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, int dir, double* gbs) {
+  if (!gbs || bytes == 0 || streams < 1 || reps < 1 || dir < 0 || dir > 2) return SET_EINVAL;
+  std::vector<cudaStream_t> ss(streams, nullptr);
+  std::vector<void*> h(2 * streams, nullptr), d(2 * streams, nullptr);
+  set_status st = SET_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && st == SET_OK) st = SET_ECUDA;
+    return e == cudaSuccess;
+  };
+  for (int i = 0; i < streams && st == SET_OK; ++i) {
+    ok(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+    ok(cudaHostAlloc(&h[2 * i], bytes, cudaHostAllocDefault));
+    ok(cudaHostAlloc(&h[2 * i + 1], bytes, cudaHostAllocDefault));
+    ok(cudaMalloc(&d[2 * i], bytes));
+    ok(cudaMalloc(&d[2 * i + 1], bytes));
+  }
+  ok(cudaEventCreate(&e0));
+  ok(cudaEventCreate(&e1));
+  if (st == SET_OK) {
+    for (int pass = 0; pass < 2 && st == SET_OK; ++pass) {  // pass 0 warms up
+      ok(cudaDeviceSynchronize());
+      ok(cudaEventRecord(e0, ss[0]));
+      for (int i = 1; i < streams; ++i) ok(cudaStreamWaitEvent(ss[i], e0, 0));
+      for (int r = 0; r < reps; ++r) {
+        const int i = r % streams;
+        if (dir != 1) ok(cudaMemcpyAsync(d[2 * i], h[2 * i], bytes, cudaMemcpyHostToDevice, ss[i]));
+        if (dir != 0) ok(cudaMemcpyAsync(h[2 * i + 1], d[2 * i + 1], bytes, cudaMemcpyDeviceToHost, ss[i]));
+      }
+      for (int i = 1; i < streams; ++i) {
+        cudaEvent_t ev;
+        ok(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ok(cudaEventRecord(ev, ss[i]));
+        ok(cudaStreamWaitEvent(ss[0], ev, 0));
+        cudaEventDestroy(ev);
+      }
+      ok(cudaEventRecord(e1, ss[0]));
+      ok(cudaEventSynchronize(e1));
+    }
+    float ms = 0.f;
+    if (ok(cudaEventElapsedTime(&ms, e0, e1)))
+      *gbs = (double)bytes * reps * (dir == 2 ? 2.0 : 1.0) / ((double)ms * 1e-3) / 1e9;
+  }
+  for (int i = 0; i < streams; ++i) {
+    if (ss[i]) cudaStreamDestroy(ss[i]);
+    if (h[2 * i]) cudaFreeHost(h[2 * i]);
+    if (h[2 * i + 1]) cudaFreeHost(h[2 * i + 1]);
+    if (d[2 * i]) cudaFree(d[2 * i]);
+    if (d[2 * i + 1]) cudaFree(d[2 * i + 1]);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
 }
 
 extern "C" int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused) {

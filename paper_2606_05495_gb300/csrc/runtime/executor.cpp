@@ -18,6 +18,18 @@ void normalize(set_config& c) {
   if (c.steal != 0) c.steal = 1;
   if (c.type_mask == 0) c.type_mask = ~0u;
   if (c.drain_timeout_ms <= 0) c.drain_timeout_ms = 30000;
+  if (c.spin_us < 0) c.spin_us = 0;
+}
+
+// Spins (plain atomic loads, no system call) for up to spin_ns while `ready` is false.
+template <class F>
+bool spin_until(F ready, uint64_t spin_ns) {
+  if (spin_ns == 0) return ready();
+  const uint64_t t_end = now_ns() + spin_ns;
+  for (int k = 0;; ++k) {
+    if (ready()) return true;
+    if ((k & 63) == 63 && now_ns() > t_end) return false;
+  }
 }
 
 }  // namespace
@@ -107,7 +119,7 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
   }
   const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);
   setk::place_job(&L, ctl);
-  if (L.end > cfg_.slot_bytes || L.persist_bytes > ctl) {
+  if (L.end > cfg_.slot_bytes || setk::control_offset(d.type) + L.persist_bytes > ctl) {
     *why = "job does not fit the slot (slot_bytes too small)";
     return SET_ENOMEM;
   }
@@ -195,12 +207,14 @@ bool Executor::find_job(uint32_t lane, JobRec& j, bool& stolen) {
 // Algorithm 2, dispatcher loop: pop a free slot (W_pool), FindJob, LaunchJob.  Waiting is a
 // futex sleep on the pool / submit signals, never a poll.
 void Executor::worker_main(int) {
+  const uint64_t spin_ns = (uint64_t)cfg_.spin_us * 1000ull;
   for (;;) {
     uint32_t tok = 0;
     for (;;) {
       const uint32_t seen = free_sig_.load();
       if (stop_.load()) return;
       if (free_->pop(tok)) break;
+      if (spin_until([&] { return free_sig_.load() != seen || stop_.load(); }, spin_ns)) continue;
       free_sig_.wait(seen, -1);
     }
     Slot& s = slots_[tok];
@@ -221,6 +235,7 @@ void Executor::worker_main(int) {
         job_sig_.wait(seen, 200 * 1000ll);
         break;
       }
+      if (spin_until([&] { return job_sig_.load() != seen || stop_.load(); }, spin_ns)) continue;
       job_sig_.wait(seen, -1);
     }
     if (!got) {

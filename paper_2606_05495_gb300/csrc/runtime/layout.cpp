@@ -34,6 +34,7 @@ bool job_sizes(uint32_t type, const uint32_t d[4], JobLayout* L) {
       L->in_bytes = 3 * px;
       L->out_bytes = ((px + 15) & ~size_t(15)) + 256 * sizeof(uint32_t) + sizeof(set_trailer);
       L->scratch_bytes = 2 * align256(px);  // gray and Gaussian images of the per-stage chain
+      L->persist_bytes = kImgHdrBytes + kImgJobStateBytes;
       return true;
     }
     case SET_JOB_MLP_LN: {
@@ -53,8 +54,10 @@ bool job_sizes(uint32_t type, const uint32_t d[4], JobLayout* L) {
 
 size_t slot_control_bytes(size_t slot_bytes) {
   // a scan job of n elements needs 8n payload bytes, so n <= slot_bytes / 8
-  return align256(kScanHdrBytes + kScanBytesPerTile * scan_tiles(slot_bytes / 8 + 1));
+  return kCtlImgBytes + align256(kScanHdrBytes + kScanBytesPerTile * scan_tiles(slot_bytes / 8 + 1));
 }
+
+size_t control_offset(uint32_t type) { return type == SET_JOB_SAXPY_SCAN_MAX ? kCtlScanOff : kCtlImgOff; }
 
 void place_job(JobLayout* L, size_t ctl) {
   L->in_off = ctl;

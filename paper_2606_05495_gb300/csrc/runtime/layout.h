@@ -25,6 +25,9 @@ bool job_sizes(uint32_t type, const uint32_t dims[4], JobLayout* L);
 // persistent state of any job whose payload fits the slot.
 size_t slot_control_bytes(size_t slot_bytes);
 
+// Offset of a job type's persistent state inside the slot control block.
+size_t control_offset(uint32_t type);
+
 // Places the job's regions after a control block of `ctl` bytes.
 void place_job(JobLayout* L, size_t ctl);
 

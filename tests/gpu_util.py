@@ -115,3 +115,24 @@ def check_scan(job):
     assert f[n] == 0.0 if n else True  # S_0 is exactly 0
     assert abs(float(f[2 * n]) - m) <= SCAN_RTOL * float(A.max()), (float(f[2 * n]), m)
     assert not f[2 * n + 1:2 * n + 4].any(), "pad after m not zero"
+
+
+def img_job(j, dims=None, **kw):
+    rgb = datagen.img_job(j, dims=dims)
+    H, W, _ = rgb.shape
+    return Job(S().SET_JOB_IMG_SOBEL_HIST, (W, H), rgb, **kw)
+
+
+def check_img(job):
+    import oracle
+    W, H = job.dims
+    s_ref, h_ref = oracle.job_img_sobel_hist(job.payload.reshape(H, W, 3))
+    o = job.out()
+    n = W * H
+    off = (n + 15) & ~15
+    got = o[:n].reshape(H, W)
+    if not np.array_equal(got, s_ref):
+        bad = np.argwhere(got != s_ref)
+        raise AssertionError(f"Sobel image mismatch at {W}x{H}: {len(bad)} px, first {bad[:5].tolist()}")
+    assert not o[n:off].any(), "pad bytes not zero"
+    assert np.array_equal(o[off:off + 1024].view(np.uint32), h_ref), f"histogram mismatch at {W}x{H}"
