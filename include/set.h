@@ -209,6 +209,21 @@ const char* set_last_error(set_ctx* ctx);
 set_status set_launch_job(const set_job_desc* job, const void* d_in, void* d_out, void* d_scratch,
                           uint64_t job_id, uint32_t slot_gen, void* stream);
 
+/* set_launch_job for a SET_JOB_SAXPY_SCAN_MAX job without any scratch buffer: for callers that
+ * cannot allocate device memory (a plugin inside a process whose GPU memory belongs to another
+ * allocator, or a latency-critical path where cudaMalloc would synchronise the device).  The paper
+ * has no counterpart; it is an addition of this library.
+ * The scratch is a file-scope static device array inside libset.so sized for n <= 16777216
+ * (2^24; 49,408 bytes on every GPU that loads the library, held until process exit); larger n
+ * returns SET_EINVAL with the limit in set_last_error(NULL).  d_in / d_out / stream as in
+ * set_launch_job.  Allocates nothing: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call clears the
+ * part of the array it uses (cudaMemsetAsync on `stream`) before its kernel.  All calls share the
+ * one array: calls that overlap on the GPU (different streams without ordering) race. */
+set_status set_launch_scan_static(const set_job_desc* job, const void* d_in, void* d_out, uint64_t job_id,
+                                  uint32_t slot_gen, void* stream);
+
 /* Number of kernels set_launch_job launches for this job (graph kernel nodes per job). */
 int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused);
 

@@ -87,6 +87,7 @@ _SIGS = {
     "set_last_error": ([c_void_p], c_char_p),
     "set_launch_job": ([POINTER(set_job_desc), c_void_p, c_void_p, c_void_p, c_uint64, c_uint32, c_void_p], c_int),
     "set_job_kernel_count": ([c_uint32, _dims, c_int], c_int),
+    "set_launch_scan_static": ([POINTER(set_job_desc), c_void_p, c_void_p, c_uint64, c_uint32, c_void_p], c_int),
     "set_run_baseline": ([c_void_p, c_int, POINTER(set_job_desc), c_size_t, POINTER(set_stats_t)], c_int),
     "set_copy_bandwidth": ([c_size_t, c_int, c_int, c_int, POINTER(c_double)], c_int),
 }

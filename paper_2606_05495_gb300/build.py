@@ -24,7 +24,8 @@ GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_sobel_hist.cu", "kernels/plan.cu"]
 CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp"]
-HEADERS = ["kernels/stages.h", "kernels/params.h", "runtime/executor.h", "runtime/sync.h", "runtime/layout.h"]
+HEADERS = ["kernels/stages.h", "kernels/params.h", "runtime/executor.h", "runtime/sync.h", "runtime/layout.h",
+           "runtime/thread_error.h"]
 
 INCLUDES = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include")]
 NVCC_FLAGS = GENCODE + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -15,6 +15,9 @@
 // launch never match; the last tile resets ticket/done/err and bumps the epoch, which leaves the
 // scratch ready for the next launch without any zeroing pass.  Every wait is bounded: a tile
 // that gives up sets SET_DEVERR_WAIT in the header, which the trailer reports.
+#include <mutex>
+
+#include "../runtime/thread_error.h"
 #include "stages.h"
 
 namespace setk {
@@ -279,4 +282,85 @@ bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   return true;
 }
 
+// ---- scan launch whose scratch needs no allocation by anyone ----
+//
+// Some callers cannot call cudaMalloc or hold a scratch buffer of their own: a plugin loaded into
+// a host process whose device memory belongs to another allocator (a serving framework, a
+// caching allocator that must not be bypassed), or a latency-critical path where an allocation
+// would synchronise the device.  For them the scan's scratch (header + per-tile status words and
+// maxima) lives in this file-scope device array, sized for n <= kStaticScanMaxN.  Every GPU that
+// loads the library holds it (49,408 bytes) until the process exits.
+namespace {
+constexpr uint32_t kStaticScanMaxN = 1u << 24;
+constexpr size_t kStaticScanBytes = kScanHdrBytes + (size_t)kScanBytesPerTile * (kStaticScanMaxN / kScanTile);
+constexpr int kStaticMaxDevices = 64;
+__device__ __align__(256) uint8_t g_static_scan_scratch[(kStaticScanBytes + 255) & ~size_t(255)];
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+}  // namespace
+
 }  // namespace setk
+
+// Host code may not use g_static_scan_scratch as an address: its device address is looked up once
+// per device with cudaGetSymbolAddress (on the first call made while that device is current).
+extern "C" set_status set_launch_scan_static(const set_job_desc* job, const void* d_in, void* d_out, uint64_t job_id,
+                                             uint32_t slot_gen, void* stream) {
+  using namespace setk;
+  if (!job || !d_in || !d_out || job->type != SET_JOB_SAXPY_SCAN_MAX) {
+    setrt::set_thread_error("set_launch_scan_static: needs a SET_JOB_SAXPY_SCAN_MAX descriptor and device in/out");
+    return SET_EINVAL;
+  }
+  const uint32_t n = job->dims[0];
+  if (n < 1 || n > kStaticScanMaxN) {
+    setrt::set_thread_error("set_launch_scan_static: n must be in 1..16777216 (size of the static scratch array)");
+    return SET_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    cudaGetLastError();
+    setrt::set_thread_error("set_launch_scan_static: no current CUDA device (or ordinal >= 64)");
+    return SET_ECUDA;
+  }
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scan_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        setrt::set_thread_error("set_launch_scan_static: cudaGetSymbolAddress of the static scratch failed");
+        return SET_ECUDA;
+      }
+      g_static_ptr[dev] = p;
+    }
+    scratch = g_static_ptr[dev];
+  }
+  JobLayout L;
+  if (!job_sizes(job->type, job->dims, &L)) return SET_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear the header and status words this call uses
+  if (cudaMemsetAsync(scratch, 0, L.persist_bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    setrt::set_thread_error("set_launch_scan_static: clearing the static scratch failed");
+    return SET_ECUDA;
+  }
+  JobPlanIn in;
+  in.type = job->type;
+  in.dims[0] = n;
+  in.scalar = job->scalar;
+  in.d_in = d_in;
+  in.d_out = d_out;
+  in.d_persist = scratch;
+  in.job_id = job_id;
+  in.slot_gen = slot_gen;
+  KernelLaunch kl[kMaxKernels];
+  int nk = 0;
+  if (!plan_saxpy_scan_max(in, L, kl, &nk)) return SET_EINVAL;
+  if (cudaLaunchKernel(kl[0].func, kl[0].grid, kl[0].block, kl[0].params, kl[0].smem, st) != cudaSuccess) {
+    cudaGetLastError();
+    setrt::set_thread_error("set_launch_scan_static: kernel launch failed");
+    return SET_ECUDA;
+  }
+  return SET_OK;
+}

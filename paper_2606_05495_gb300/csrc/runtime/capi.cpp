@@ -5,6 +5,7 @@
 #include "executor.h"
 #include "layout.h"
 #include "set.h"
+#include "thread_error.h"
 
 struct set_ctx {
   setrt::Executor* ex;
@@ -18,6 +19,10 @@ set_status ctx_less(set_status st, const std::string& msg) {
   return st;
 }
 }  // namespace
+
+namespace setrt {
+void set_thread_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace setrt
 
 extern "C" {
 
