@@ -53,11 +53,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["set", "reference"], default="set")
     p.add_argument("--jobs", type=int, default=4096)
-    p.add_argument("--streams", type=int, default=8)
-    p.add_argument("--workers", type=int, default=8)
-    p.add_argument("--ring", type=int, default=2)
+    p.add_argument("--streams", type=int, default=16)
+    p.add_argument("--workers", type=int, default=1, help="host dispatch threads (1 is fastest on Grace)")
+    p.add_argument("--ring", type=int, default=4)
+    p.add_argument("--cb-mode", type=int, default=0)
+    p.add_argument("--cb-every", type=int, default=8, help="jobs per completion callback and lane")
     p.add_argument("--no-baselines", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
+                   help="only launch the dominant kernel this many times (for ncu), then exit")
     return p.parse_args()
 
 
@@ -273,8 +277,10 @@ def copy_rates(S, job_in: int, job_out: int, streams: int, reps: int = 2048):
 
 
 def kernel_time(S, w: Workload, launches: int = 512):
-    """Average duration (us) of the saxpy_scan_max kernel launched alone per job, CUDA events
-    around each launch on the launching stream, inputs cycling over the > L2 resident set."""
+    """Average duration (us) of the saxpy_scan_max kernel launched alone per job: CUDA events
+    around each launch on the launching stream, inputs cycling over the > L2 resident set.  A
+    sleep kernel holds the stream while all launches are enqueued, so the GPU never waits for the
+    host between them and each event pair brackets device time only."""
     t = _torch()
     s = t.cuda.Stream()
     scratch = t.zeros(S.set_job_scratch_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), dtype=t.uint8,
@@ -285,6 +291,8 @@ def kernel_time(S, w: Workload, launches: int = 512):
         for k in range(32):
             d = w.descs_dev[k % nj]
             S.check(S.set_launch_job(ctypes.byref(d), d.in_, d.out, scratch.data_ptr(), k, 0, s.cuda_stream), "launch")
+        s.synchronize()
+        t.cuda._sleep(int(2e9 * 20e-6 * launches))  # ~20 us of host enqueue time per launch
         for k in range(launches):
             d = w.descs_dev[(k * 7) % nj]
             evs[k][0].record(s)
@@ -295,6 +303,19 @@ def kernel_time(S, w: Workload, launches: int = 512):
     return statistics.mean(ts), statistics.median(ts)
 
 
+def kernel_only(S, w: Workload, launches: int):
+    """Launches the dominant kernel alone `launches` times over the resident inputs (profiling)."""
+    t = _torch()
+    scratch = t.zeros(S.set_job_scratch_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), dtype=t.uint8,
+                      device=w.d_in.device)
+    s = t.cuda.current_stream().cuda_stream
+    for k in range(launches):
+        d = w.descs_dev[(k * 7) % len(w.ids)]
+        S.check(S.set_launch_job(ctypes.byref(d), d.in_, d.out, scratch.data_ptr(), k, 0, s), "set_launch_job")
+    t.cuda.synchronize()
+    print(json.dumps({"kernel_only": "saxpy_scan_max_kernel", "launches": launches}), flush=True)
+
+
 def run_set(args, d: Dist):
     t = _torch()
     import paper_2606_05495_gb300 as S
@@ -302,9 +323,13 @@ def run_set(args, d: Dist):
     dev_index = d.local if t.cuda.is_available() else 0
     t.cuda.set_device(dev_index)
     w = Workload(S, shard(args.jobs, d.rank), dev_index)
+    if args.kernel_only:
+        kernel_only(S, w, args.kernel_only)
+        return
     nj = len(w.ids)
     cfg = dict(num_streams=args.streams, num_workers=args.workers, slot_bytes=S.set_job_slot_bytes(
-        S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), ring_depth=args.ring, device=dev_index)
+        S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), ring_depth=args.ring, cb_mode=args.cb_mode,
+        cb_every=args.cb_every, device=dev_index)
 
     # value: inputs and outputs resident in HBM
     ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
@@ -312,6 +337,12 @@ def run_set(args, d: Dist):
     ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d)
     clk = clocks.stop()
     S.set_destroy(ctx_dev)
+
+    # e2e with one completion callback per job (Algorithm 3 as written), for reference
+    c1 = dict(cfg, cb_every=1)
+    ctx1 = S.create(S.default_config(io_mode=S.SET_IO_HOST, **c1))
+    ms_host1, st_host1 = timed(S, ctx1, w.descs_host, nj, argparse.Namespace(warmup=2, steps=min(3, args.steps)), d)
+    S.set_destroy(ctx1)
 
     # e2e: pinned host buffers, H2D/D2H inside the timed region
     ctx = S.create(S.default_config(io_mode=S.SET_IO_HOST, **cfg))
@@ -328,6 +359,18 @@ def run_set(args, d: Dist):
             best = sorted(runs, key=lambda r: r["jobs_per_s"])[len(runs) // 2]
             baselines[name] = {"jobs_per_s": best["jobs_per_s"], "p50_us": best["p50_us"], "p99_us": best["p99_us"],
                                "streams": 1 if kind == S.SET_BASE_SYNC else args.streams}
+    # one CUPTI-traced step of each (untimed): device-timeline gaps (Sec. 3.2, Eq. 2-4)
+    traces = {}
+    tr = S.set_trace_summary()
+    if S.set_trace_start() == S.SET_OK:
+        run_step(S, ctx, w.descs_host, nj)
+        S.set_trace_stop(ctypes.byref(tr))
+        traces["set"] = tr.as_dict()
+        if not args.no_baselines and S.set_trace_start() == S.SET_OK:
+            st = S.set_stats_t()
+            S.set_run_baseline(ctx, S.SET_BASE_BATCH_SYNC, w.descs_host, nj, ctypes.byref(st))
+            S.set_trace_stop(ctypes.byref(tr))
+            traces["batch_sync_graph"] = tr.as_dict()
     S.set_destroy(ctx)
 
     k_mean_us, k_med_us = kernel_time(S, w)
@@ -347,7 +390,9 @@ def run_set(args, d: Dist):
     t_h2d = nj * JOB_IN / (rates["h2d_gbs"] * 1e9)
     t_d2h = nj * JOB_OUT / (rates["d2h_gbs"] * 1e9)
     t_bi = nj * (JOB_IN + JOB_OUT) / (rates["bidir_total_gbs"] * 1e9)
-    t_sm = nj * k_mean_us * 1e-6
+    k_exec_us = traces.get("set", {}).get("top_kernel_mean_us") or k_mean_us
+    sms = t.cuda.get_device_properties(dev_index).multi_processor_count
+    t_sm = nj * k_exec_us * 1e-6 * 16 / sms  # 16 CTAs per job, one per SM: the share of SM time
     bound_s = max(t_h2d, t_d2h, t_bi, t_sm)
     if d.rank != 0:
         return
@@ -357,12 +402,15 @@ def run_set(args, d: Dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64 inputs, resident before timing)",
         "config": {"workload": "scan jobs (saxpy -> exclusive scan -> max|S|), n=65536 fp32, 4096 jobs per GPU",
                    "jobs_per_step": nj * world, "streams": args.streams, "workers": args.workers,
-                   "ring_depth": args.ring, "steal": True, "io": "HBM-resident in/out (SET_IO_DEVICE)",
+                   "ring_depth": args.ring, "cb_mode": args.cb_mode, "cb_every": args.cb_every, "steal": True,
+                   "io": "HBM-resident in/out (SET_IO_DEVICE)",
                    "l2": "inputs 2 GiB > L2 per step (no flush needed)", "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
                 "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
                 "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
-                "steals": st_host["steals"]},
+                "steals": st_host["steals"],
+                "per_job_callbacks": {"value": world * nj / (ms_host1 * 1e-3), "p99_us": st_host1["p99_us"],
+                                      "note": "cb_every=1: one completion callback per job"}},
         "gpu_launches": args.steps * nj * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "saxpy_scan_max_kernel",
@@ -371,7 +419,11 @@ def run_set(args, d: Dist):
         "pipeline": {"copy_rates_gbs": rates, "bound_jobs_per_s": nj / bound_s,
                      "e2e_frac_of_bound": (nj / (ms_host * 1e-3)) / (nj / bound_s),
                      "terms_ms": {"h2d": t_h2d * 1e3, "d2h": t_d2h * 1e3, "bidir": t_bi * 1e3, "sm": t_sm * 1e3}},
-        "p99_us": st_host["p99_us"], "mean_kernel_gap_us": None,
+        "p99_us": st_host["p99_us"],
+        "mean_kernel_gap_us": traces.get("set", {}).get("mean_kernel_gap_us"),
+        "trace": {k: {f: v[f] for f in ("kernels", "memcpys", "span_us", "kernel_busy_us", "copy_busy_us",
+                                        "idle_frac", "mean_kernel_gap_us", "max_kernel_gap_us", "top_kernel_mean_us")}
+                  for k, v in traces.items()},
         "baselines": baselines, "clocks": clk,
     }
     if not args.no_cpu:

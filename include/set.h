@@ -132,9 +132,22 @@ typedef struct {
   int drain_timeout_ms; /* set_destroy waits at most this long for jobs in flight (default 30000) */
   int cb_mode;         /* 0 (default): completion callback on a per-lane callback stream that waits
                           on an event recorded behind the graph (the lane never waits on the host);
-                          1: cudaLaunchHostFunc directly on the lane stream */
+                          1: cudaLaunchHostFunc directly on the lane stream;
+                          2: a host node at the end of every slot's graph (no extra call per job) */
   int spin_us;         /* dispatch workers spin this long on an empty pool / queue before they
                           sleep on a futex (default 50; 0 = sleep at once) */
+  int cb_every;        /* cb_mode 0/1: attach one completion callback per this many jobs of a lane
+                          (it completes the whole group in stream order; default 1 = one per job).
+                          Groups are closed early whenever a dispatch worker would wait. */
+  int batch_max;       /* batched form: up to this many queued jobs of one batchable type (image,
+                          MLP) share one launch of packed persistent kernels (default 1 = off) */
+  int img_ctas_per_sm; /* batched image kernel: persistent CTAs per SM (default 4) */
+  int img_tile;        /* batched image kernel tile: 0 = 32x128 (default), 1 = 16x256, 2 = 64x64 */
+  size_t arena_bytes;  /* serving form: 0 (default) = every job uses its slot's memory; > 0 = each
+                          job's in/out/scratch is allocated at dispatch from a device arena of this
+                          size (buddy blocks, 64 KiB minimum) and freed by its completion callback,
+                          so jobs are admitted by free memory; slots then hold only the kernels'
+                          control state and slot_bytes only bounds the largest job */
 } set_config;
 
 typedef struct {
@@ -147,6 +160,8 @@ typedef struct {
   double p50_us, p99_us, max_us; /* submit -> completion callback latency */
   double mean_update_us;    /* host time of UpdateGraphParams per job */
   double mean_launch_us;    /* host time of graph launch + callback chaining per job */
+  uint64_t mem_waits;       /* arena mode: dispatches that waited for free memory */
+  uint64_t arena_peak_bytes;/* arena mode: peak bytes allocated */
 } set_stats_t;
 
 /* ---- sizes ---- */
@@ -214,7 +229,7 @@ set_status set_launch_job(const set_job_desc* job, const void* d_in, void* d_out
  * allocator, or a latency-critical path where cudaMalloc would synchronise the device).  The paper
  * has no counterpart; it is an addition of this library.
  * The scratch is a file-scope static device array inside libset.so sized for n <= 16777216
- * (2^24; 49,408 bytes on every GPU that loads the library, held until process exit); larger n
+ * (2^24; 65,792 bytes on every GPU that loads the library, held until process exit); larger n
  * returns SET_EINVAL with the limit in set_last_error(NULL).  d_in / d_out / stream as in
  * set_launch_job.  Allocates nothing: no cudaMalloc, no cudaFree.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
@@ -235,6 +250,31 @@ int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused);
  * device.  Used for the pipeline bound of the measured throughput. */
 set_status set_copy_bandwidth(size_t bytes, int streams, int reps, int dir, double* gbs);
 
+/* Device-timeline summary of a CUPTI activity trace (Sec. 3.2: the gaps between operations that
+ * Eq. 2-4 attribute to scheduling).  Times in microseconds. */
+typedef struct {
+  uint64_t kernels, memcpys;   /* records traced */
+  double span_us;              /* first start to last end over kernels and copies */
+  double kernel_busy_us;       /* union of kernel intervals */
+  double copy_busy_us;         /* union of copy intervals */
+  double any_busy_us;          /* union of both */
+  double idle_frac;            /* 1 - any_busy / span: the device-idle share of the span */
+  double mean_kernel_gap_us;   /* mean over consecutive kernels (by start) of the idle time
+                                  between the end of all earlier kernels and the next start */
+  double max_kernel_gap_us;
+  char top_kernel[128];        /* kernel name with the largest total time */
+  uint64_t top_kernel_launches;
+  double top_kernel_mean_us;   /* its mean duration */
+  double top_kernel_share;     /* its share of total kernel time */
+} set_trace_summary;
+
+/* Starts recording kernels and copies of this process with CUPTI (libcupti is loaded with dlopen
+ * on first use; SET_EINVAL if it cannot be found).  Tracing adds host overhead per launch: time
+ * throughput without it. */
+set_status set_trace_start(void);
+/* Stops recording, flushes every record and fills *out. */
+set_status set_trace_stop(set_trace_summary* out);
+
 /* ---- baselines run on the same kernels (Sec. 5.1.3) ---- */
 
 typedef enum {
@@ -244,9 +284,42 @@ typedef enum {
 } set_baseline_kind;
 
 /* Runs all n jobs under a baseline model with the context's lanes, slots and graph execs (the
- * context's own dispatch threads stay idle).  Fills *out like set_stats. */
+ * context's own dispatch threads stay idle).  Fills *out like set_stats.  Jobs with a non-zero
+ * t_arrival_ns are not started before that time: SET_BASE_BATCH_SYNC then forms each batch from
+ * the jobs that have arrived (at least one, at most num_streams). */
 set_status set_run_baseline(set_ctx* ctx, int kind, const set_job_desc* jobs, size_t n,
                             set_stats_t* out);
+
+/* ---- autotuner of the batched form ---- */
+
+typedef struct {
+  int batch_max;        /* jobs per launch chosen (<= the context's batch_max) */
+  int img_tile;         /* image tile variant chosen */
+  int img_ctas_per_sm;  /* persistent CTAs per SM chosen */
+  int candidates;       /* candidates timed */
+  double jobs_per_s;    /* device throughput of the packed kernels with the choice */
+  double single_jobs_per_s; /* the same sample one job per launch */
+} set_tune_result;
+
+/* Times the packed kernels of `type` (image or MLP) on the sample jobs for every candidate
+ * (jobs per launch 1..batch_max in powers of two; for images also tile 0..2 and 1, 2, 4, 8 CTAs
+ * per SM), with CUDA events around the kernels only, and keeps the smallest jobs-per-launch within
+ * 5% of the best throughput (less waiting to fill batches).  The choice applies to the context's
+ * later dispatches.  The context must be idle; allocates and frees a scratch buffer. */
+set_status set_autotune(set_ctx* ctx, uint32_t type, const set_job_desc* sample, size_t n, set_tune_result* out);
+
+/* ---- serving loop (continuous batching) ---- */
+
+#define SET_SERVE_SET 0        /* jobs go through set_submit as they arrive (the SET executor) */
+#define SET_SERVE_BATCH_SYNC 1 /* the same arrivals under SET_BASE_BATCH_SYNC */
+
+/* Request loop: job i arrives at (start + arrival_ns[i]) on CLOCK_MONOTONIC, arrival_ns ascending.
+ * SET_SERVE_SET submits each job at its arrival time (t_arrival_ns set, blocking while every queue
+ * is full) and waits for all; jobs that arrive while others run are admitted as slots and arena
+ * memory free up and overlap on the device.  SET_SERVE_BATCH_SYNC runs the same arrivals through
+ * the batch-synchronous baseline.  *out gets throughput and arrival -> completion latency. */
+set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uint64_t* arrival_ns, size_t n,
+                     set_stats_t* out);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,7 @@ SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX, SET_JOB_IMG_SOBEL_HIST, SET_JOB_MLP_L
 SET_F_NONBLOCK = 0x1
 SET_IO_HOST, SET_IO_DEVICE = 0, 1
 SET_BASE_SYNC, SET_BASE_BATCH_SYNC = 1, 2
+SET_SERVE_SET, SET_SERVE_BATCH_SYNC = 0, 1
 SET_TRAILER_MAGIC = 0x5E7C
 SET_DEVERR_WAIT = 0x1
 
@@ -45,14 +46,37 @@ class set_config(ctypes.Structure):
     _fields_ = [("num_streams", c_int), ("num_workers", c_int), ("slot_bytes", c_size_t), ("ring_depth", c_int),
                 ("queue_capacity", c_int), ("steal", c_int), ("io_mode", c_int), ("img_fused", c_int),
                 ("pool", c_void_p), ("pool_bytes", c_size_t), ("type_mask", c_uint32), ("device", c_int),
-                ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int)]
+                ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int), ("cb_every", c_int),
+                ("batch_max", c_int), ("img_ctas_per_sm", c_int), ("img_tile", c_int),
+                ("arena_bytes", c_size_t)]
 
 
 class set_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("failed", c_uint64), ("steals", c_uint64),
                 ("updates", c_uint64), ("canary_errors", c_uint64), ("elapsed_s", c_double),
                 ("jobs_per_s", c_double), ("p50_us", c_double), ("p99_us", c_double), ("max_us", c_double),
-                ("mean_update_us", c_double), ("mean_launch_us", c_double)]
+                ("mean_update_us", c_double), ("mean_launch_us", c_double), ("mem_waits", c_uint64),
+                ("arena_peak_bytes", c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class set_trace_summary(ctypes.Structure):
+    _fields_ = [("kernels", c_uint64), ("memcpys", c_uint64), ("span_us", c_double), ("kernel_busy_us", c_double),
+                ("copy_busy_us", c_double), ("any_busy_us", c_double), ("idle_frac", c_double),
+                ("mean_kernel_gap_us", c_double), ("max_kernel_gap_us", c_double), ("top_kernel", ctypes.c_char * 128),
+                ("top_kernel_launches", c_uint64), ("top_kernel_mean_us", c_double), ("top_kernel_share", c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["top_kernel"] = self.top_kernel.decode(errors="replace")
+        return d
+
+
+class set_tune_result(ctypes.Structure):
+    _fields_ = [("batch_max", c_int), ("img_tile", c_int), ("img_ctas_per_sm", c_int), ("candidates", c_int),
+                ("jobs_per_s", c_double), ("single_jobs_per_s", c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -90,6 +114,10 @@ _SIGS = {
     "set_launch_scan_static": ([POINTER(set_job_desc), c_void_p, c_void_p, c_uint64, c_uint32, c_void_p], c_int),
     "set_run_baseline": ([c_void_p, c_int, POINTER(set_job_desc), c_size_t, POINTER(set_stats_t)], c_int),
     "set_copy_bandwidth": ([c_size_t, c_int, c_int, c_int, POINTER(c_double)], c_int),
+    "set_trace_start": ([], c_int),
+    "set_autotune": ([c_void_p, c_uint32, POINTER(set_job_desc), c_size_t, POINTER(set_tune_result)], c_int),
+    "set_serve": ([c_void_p, c_int, POINTER(set_job_desc), POINTER(c_uint64), c_size_t, POINTER(set_stats_t)], c_int),
+    "set_trace_stop": ([POINTER(set_trace_summary)], c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)

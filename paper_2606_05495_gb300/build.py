@@ -22,10 +22,12 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_sobel_hist.cu", "kernels/plan.cu"]
-CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp"]
-HEADERS = ["kernels/stages.h", "kernels/params.h", "runtime/executor.h", "runtime/sync.h", "runtime/layout.h",
-           "runtime/thread_error.h"]
+CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_sobel_hist.cu",
+              "kernels/mlp_ln.cu", "kernels/plan.cu"]
+CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp",
+               "runtime/trace.cpp"]
+HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "runtime/executor.h", "runtime/sync.h",
+           "runtime/layout.h", "runtime/thread_error.h"]
 
 INCLUDES = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include")]
 NVCC_FLAGS = GENCODE + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -75,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         _run([NVCC] + GENCODE + ["-shared", "-cudart", "shared", "-o", tmp] + objs +
-             ["-Xlinker", "-rpath=" + os.path.join(CUDA_HOME, "lib64"), "-lpthread"])
+             ["-Xlinker", "-rpath=" + os.path.join(CUDA_HOME, "lib64"), "-lpthread", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -21,6 +21,9 @@
 // CTA that completes the job's last item (items-done counter) copies the accumulator into the
 // job's output, zeroes it and resets the counter, then writes the pad and the trailer.  The last
 // CTA to leave resets the ticket.  No zeroing pass, no memset node.
+#include <algorithm>
+#include <cstring>
+
 #include "stages.h"
 
 namespace setk {
@@ -47,6 +50,8 @@ struct ImgJobDev {
   uint32_t slot_gen, npad;
   uint32_t pad_;
 };
+
+static_assert(sizeof(ImgJobDev) <= kImgJobDescBytes, "job descriptor fits its table stride");
 
 struct ImgHdr {
   uint32_t ticket;
@@ -124,12 +129,13 @@ __device__ void gauss_tile(uint8_t (*q_s)[QP], const uint8_t (*g_s)[GP], uint16_
   }
 }
 
-// Sobel of the tile's output pixels: thread t computes 16 pixels of row t/8.  q_s[r][c] holds
-// q[cl(y0 - 1 + r)][cl(x0 - 1 + c)].  Writes the pixels inside the image and counts them.
-template <int QP>
+// Sobel of the tile's output pixels: thread t computes 16 pixels of row t / (TW / 16).  q_s[r][c]
+// holds q[cl(y0 - 1 + r)][cl(x0 - 1 + c)].  Writes the pixels inside the image and counts them.
+template <int QP, int TW = kTW>
 __device__ void sobel_tile(const uint8_t (*q_s)[QP], uint8_t* __restrict__ out, uint32_t (*whist)[256], int W, int H,
                            int y0, int x0, bool vec) {
-  const int r = threadIdx.x >> 3, s = (threadIdx.x & 7) << 4;
+  constexpr int kSegs = TW / 16;
+  const int r = threadIdx.x / kSegs, s = (threadIdx.x % kSegs) << 4;
   const int y = y0 + r;
   if (y >= H || x0 + s >= W) return;
   const uint8_t* a = q_s[r] + s;  // row y-1, columns x-1 ..
@@ -197,8 +203,12 @@ __device__ void finish_item(const ImgJobDev& j, uint32_t (*whist)[256], uint32_t
   }
 }
 
+// Tile shapes of the fused kernel (rows x columns, 4096 outputs for 256 threads x 16 pixels); the
+// work item is a band of RB rows x up to kImgChunkCols columns.  The autotuner picks one.
+template <int RB, int TW>
 __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs a) {
-  constexpr int GR = kRB + 6, GC = kTW + 6, QR = kRB + 2, QC = kTW + 2, P = kTW + 8;
+  static_assert(RB * TW == kThreads * 16, "one 16-pixel segment per thread");
+  constexpr int GR = RB + 6, GC = TW + 6, QR = RB + 2, QC = TW + 2, P = TW + 8;
   __shared__ __align__(16) uint8_t g_s[GR][P];
   __shared__ __align__(16) uint16_t v_s[QR][P];
   __shared__ __align__(16) uint8_t q_s[QR][P];
@@ -218,15 +228,15 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
     const int W = (int)j.W, H = (int)j.H;
     const uint32_t local = item - j.item0;
     const int band = (int)(local / j.chunks), chunk = (int)(local - (uint32_t)band * j.chunks);
-    const int y0 = band * kRB;
+    const int y0 = band * RB;
     const int xa = chunk * kImgChunkCols, xb = min(W, xa + kImgChunkCols);
     const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
-    for (int x0 = xa; x0 < xb; x0 += kTW) {
+    for (int x0 = xa; x0 < xb; x0 += TW) {
       stage_gray<GR, GC, P>(g_s, j.rgb, W, H, y0 - 3, x0 - 3);
       __syncthreads();
       gauss_tile<QR, QC, GC, P, P, P>(q_s, g_s, v_s, W, H, y0 - 1, x0 - 1, y0 - 3, x0 - 3);
       __syncthreads();
-      sobel_tile<P>(q_s, j.out, whist, W, H, y0, x0, vec);
+      sobel_tile<P, TW>(q_s, j.out, whist, W, H, y0, x0, vec);
       __syncthreads();
     }
     finish_item(j, whist, &s_flag);
@@ -309,9 +319,22 @@ __global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArg
   }
 }
 
-uint32_t items_of(uint32_t W, uint32_t H, uint32_t* chunks) {
+constexpr int kTileRows[3] = {32, 16, 64};  // tile variants: 32x128, 16x256, 64x64
+
+uint32_t items_of(uint32_t W, uint32_t H, uint32_t* chunks, int rows = kRB) {
   *chunks = (W + kImgChunkCols - 1) / kImgChunkCols;
-  return ((H + kRB - 1) / kRB) * *chunks;
+  return ((H + rows - 1) / rows) * *chunks;
+}
+
+const void* fused_func(int variant) {
+  switch (variant) {
+    case 1:
+      return reinterpret_cast<const void*>(&img_fused_kernel<16, 256>);
+    case 2:
+      return reinterpret_cast<const void*>(&img_fused_kernel<64, 64>);
+    default:
+      return reinterpret_cast<const void*>(&img_fused_kernel<32, 128>);
+  }
 }
 
 ImgJobDev job_dev(const JobPlanIn& in, const JobLayout& L) {
@@ -359,7 +382,7 @@ bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   const uint32_t grid = std::min<uint32_t>(j.nitems, (uint32_t)sm_count() * 4);
   if (in.img_fused) {
     KernelLaunch& k = kl[0];
-    k.func = reinterpret_cast<const void*>(&img_fused_kernel);
+    k.func = fused_func(0);
     k.grid = dim3(grid);
     k.block = dim3(kThreads);
     k.deps = 0;
@@ -396,7 +419,50 @@ bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   return true;
 }
 
-// Batched form: one fused launch over many image jobs (device job table prepared by the caller).
-size_t img_batch_table_bytes(uint32_t njobs) { return sizeof(ImgJobDev) * njobs; }
+// Batched form: one persistent fused launch over nb image jobs.  The table region of the batch
+// block holds {header (ticket 0), nb job descriptors, nb zeroed histogram accumulators}; it is
+// written here into the host staging buffer and copied in by the batch graph's first node.
+bool plan_img_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_t* d_block, uint8_t* h_table,
+                    uint32_t slot_gen, int ctas_per_sm, int variant, KernelLaunch* kl, int* nk) {
+  if (variant < 0 || variant > 2) variant = 0;
+  std::memset(h_table, 0, L.table_bytes);
+  const size_t desc_off = kImgHdrBytes, acc_off = kImgHdrBytes + (size_t)nb * kImgJobDescBytes;
+  uint32_t item = 0;
+  for (int j = 0; j < nb; ++j) {
+    const uint32_t W = items[j].dims[0], H = items[j].dims[1];
+    const size_t px = (size_t)W * H, hist_off = (px + 15) & ~size_t(15);
+    uint8_t* out = d_block + L.out_off[j];
+    ImgJobDev jd{};
+    jd.rgb = d_block + L.in_off[j];
+    jd.out = out;
+    jd.pad = out + px;
+    jd.npad = (uint32_t)(hist_off - px);
+    jd.hist = reinterpret_cast<uint32_t*>(out + hist_off);
+    jd.trailer = reinterpret_cast<set_trailer*>(out + L.out_bytes[j] - sizeof(set_trailer));
+    jd.acc = reinterpret_cast<uint32_t*>(d_block + acc_off + (size_t)j * kImgJobStateBytes);
+    jd.job_id = items[j].job_id;
+    jd.W = W;
+    jd.H = H;
+    jd.item0 = item;
+    jd.nitems = items_of(W, H, &jd.chunks, kTileRows[variant]);
+    jd.slot_gen = slot_gen;
+    item += jd.nitems;
+    std::memcpy(h_table + desc_off + (size_t)j * sizeof(ImgJobDev), &jd, sizeof jd);
+  }
+  ImgFusedArgs fa{};
+  fa.table = reinterpret_cast<const ImgJobDev*>(d_block + desc_off);
+  fa.hdr = reinterpret_cast<ImgHdr*>(d_block);
+  fa.njobs = (uint32_t)nb;
+  fa.total_items = item;
+  KernelLaunch& k = kl[0];
+  k.func = fused_func(variant);
+  k.grid = dim3(std::min<uint32_t>(item, (uint32_t)(sm_count() * std::max(1, ctas_per_sm))));
+  k.block = dim3(kThreads);
+  k.smem = 0;
+  k.deps = 0;
+  set_args(k, fa);
+  *nk = 1;
+  return true;
+}
 
 }  // namespace setk

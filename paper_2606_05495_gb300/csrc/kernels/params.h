@@ -11,22 +11,26 @@ constexpr int kBlurMaxH = 65535;
 constexpr uint32_t kScanTile = 4096;       // elements per scan tile (256 threads x 16)
 constexpr uint32_t kScanMaxN = 1u << 26;
 constexpr uint32_t kScanHdrBytes = 64;     // {ticket, done, epoch, err} + padding
-constexpr uint32_t kScanBytesPerTile = 12; // 64-bit status word + float tile max
+constexpr uint32_t kScanBytesPerTile = 16; // 64-bit status word + 64-bit tile max word
 
 constexpr int kImgMaxSide = 4096;
 constexpr uint32_t kImgHdrBytes = 64;        // {ticket} + padding
 constexpr uint32_t kImgJobStateBytes = 1152; // hist accumulator [256] u32 + items-done counter, padded
+constexpr uint32_t kImgJobDescBytes = 128;   // device job descriptor of the fused kernel
 constexpr int kImgBandRows = 32;             // output rows of one work item
 constexpr int kImgChunkCols = 512;           // output columns of one work item
 constexpr int kImgMaxBatch = 4096;           // jobs of one batched launch
 
 // Slot control block: [image state (fixed) | scan state (grows with the slot)].
 constexpr uint32_t kCtlImgOff = 0;
+constexpr uint32_t kCtlMlpOff = 1536;        // MLP job state {err, done} inside the fixed region
 constexpr uint32_t kCtlImgBytes = 2048;
 constexpr uint32_t kCtlScanOff = kCtlImgBytes;
 
 constexpr int kMlpD = 1024;
 constexpr int kMlpF = 4096;
 constexpr int kMlpMaxM = 256;
+constexpr uint32_t kMlpCtlBytes = 64;
+constexpr uint32_t kMlpTrailerRecBytes = 32; // batch: {trailer pointer, job id, slot generation}
 
 }  // namespace setk

@@ -13,6 +13,8 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
       return plan_saxpy_scan_max(in, L, kl, nk);
     case SET_JOB_IMG_SOBEL_HIST:
       return plan_img_sobel_hist(in, L, kl, nk);
+    case SET_JOB_MLP_LN:
+      return plan_mlp_ln(in, L, kl, nk);
     default:
       return false;
   }
@@ -20,6 +22,7 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
 
 cudaError_t kernels_init() {
   cudaError_t e = blur_hist_init();
+  if (e == cudaSuccess) e = mlp_init();
   return e;
 }
 

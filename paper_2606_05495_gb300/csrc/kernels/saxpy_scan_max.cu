@@ -1,20 +1,25 @@
 // saxpy_scan_max.cu -- scan job: z = fmaf(a, x, y), S = exclusive prefix sum of z, m = max|S_i|,
 // in one single-pass kernel.
 //
-// Tiles of 4096 elements (256 threads x 16 contiguous elements, 16-byte loads and stores).
-// Tiles take a ticket from an atomic counter so that tile ids follow scheduling order, and
-// resolve their prefix with decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
-// Scan with Decoupled Look-back", 2016): each tile publishes its aggregate, then one warp reads
-// the status words of 32 predecessors per round trip and sums back to the nearest inclusive
-// prefix.  Inside a tile the scan is
-// thread-serial, then warp-shuffle, then across the 8 warps.  Each tile also publishes its
-// max|S|; the last tile to finish (done counter) reduces them into m and writes the trailer.
+// Tiles of 4096 elements (256 threads x 16 contiguous elements, 16-byte loads and stores), one
+// per block in block-index order, resolve their prefix with decoupled look-back (Merrill &
+// Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016): each tile
+// publishes its aggregate, then one warp reads the status words of 32 predecessors per round trip
+// and sums back to the nearest inclusive prefix.  Inside a tile the scan is thread-serial, then
+// warp-shuffle, then across the 8 warps.
 //
-// Scratch: a 64-byte header {ticket, done, epoch, err} followed by one 64-bit status word and
-// one float per tile.  Status words carry the header's epoch, so stale words of an earlier
-// launch never match; the last tile resets ticket/done/err and bumps the epoch, which leaves the
-// scratch ready for the next launch without any zeroing pass.  Every wait is bounded: a tile
-// that gives up sets SET_DEVERR_WAIT in the header, which the trailer reports.
+// Latency is the cost of a 1 MiB job, so the kernel keeps its chain of dependent global round
+// trips short: z stays in registers until the prefix is known (nothing has to drain before a
+// status word is published), status words are self-contained (relaxed stores and loads, no
+// fences), and instead of a done counter every tile publishes an epoch-tagged max|S| word that
+// the last tile gathers with one warp to write m and the trailer.
+//
+// Scratch: a 64-byte header {unused, unused, epoch, err}, then per tile one 64-bit status word
+// {epoch, flag, value} and one 64-bit max word {epoch, max|S| bits}.  Words carry the header's
+// epoch, so stale words of an earlier launch never match; the last tile bumps the epoch and
+// clears err once every tile has published, which leaves the scratch ready for the next launch
+// without a zeroing pass.  Every wait is bounded: a tile that gives up sets SET_DEVERR_WAIT in the
+// header, which the trailer reports.
 #include <mutex>
 
 #include "../runtime/thread_error.h"
@@ -33,10 +38,11 @@ constexpr int kSpinLimit = 1 << 22;  // ~0.1-0.4 s with the back-off below
 constexpr uint32_t kFlagAgg = 1, kFlagInc = 2;
 
 struct ScanHdr {
-  uint32_t ticket, done, epoch, err;
+  uint32_t unused0, unused1, epoch, err;
   uint32_t pad[12];
 };
 static_assert(sizeof(ScanHdr) == kScanHdrBytes, "scan header size shared with the layout code");
+static_assert(kScanBytesPerTile == 16, "status word + max word per tile");
 
 struct ScanArgs {
   const float* x;
@@ -52,38 +58,39 @@ struct ScanArgs {
   uint32_t slot_gen;
 };
 
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint64_t status_word(uint32_t epoch, uint32_t flag, float v) {
   return ((uint64_t)(epoch & 0x3FFFFFFFu) << 34) | ((uint64_t)flag << 32) | (uint64_t)__float_as_uint(v);
 }
+__device__ __forceinline__ uint64_t max_word(uint32_t epoch, float m) {
+  return ((uint64_t)(epoch | 0x80000000u) << 32) | (uint64_t)__float_as_uint(m);
+}
 
 __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs p) {
-  __shared__ uint32_t s_tile, s_epoch, s_last;
   __shared__ float s_wsum[kWarps], s_wexcl[kWarps], s_wmax[kWarps];
-  __shared__ float s_prefix, s_agg;
+  __shared__ float s_prefix;
   ScanHdr* hdr = reinterpret_cast<ScanHdr*>(p.scratch);
   uint64_t* status = reinterpret_cast<uint64_t*>(p.scratch + sizeof(ScanHdr));
-  float* tmax = reinterpret_cast<float*>(status + p.T);
+  uint64_t* maxw = status + p.T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  if (tid == 0) {
-    s_tile = atomicAdd(&hdr->ticket, 1u);
-    s_epoch = *reinterpret_cast<volatile uint32_t*>(&hdr->epoch) & 0x3FFFFFFFu;
-  }
-  __syncthreads();
-  const uint32_t tile = s_tile, epoch = s_epoch;
+  // tile = blockIdx.x: blocks are dispatched in index order, so every tile a look-back waits for
+  // has started.  The epoch load is issued first and only consumed by the look-back, so its
+  // latency overlaps the data loads.
+  const uint32_t tile = blockIdx.x;
+  const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&hdr->epoch) & 0x3FFFFFFFu;
   const uint32_t n = p.n;
   const size_t base = (size_t)tile * kTile + (size_t)tid * kPer;
   const bool vec = (n & 3u) == 0 && base + kPer <= n;
 
-  // saxpy: z = fmaf(a, x, y), written once
+  // saxpy: z = fmaf(a, x, y), kept in registers until the prefix is known
   float z[kPer];
   if (vec) {
 #pragma unroll
@@ -94,17 +101,12 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
       z[4 * q + 1] = fmaf(p.a, xv.y, yv.y);
       z[4 * q + 2] = fmaf(p.a, xv.z, yv.z);
       z[4 * q + 3] = fmaf(p.a, xv.w, yv.w);
-      reinterpret_cast<float4*>(p.z + base)[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
     }
   } else {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const size_t i = base + k;
-      z[k] = 0.f;
-      if (i < n) {
-        z[k] = fmaf(p.a, p.x[i], p.y[i]);
-        p.z[i] = z[k];
-      }
+      z[k] = i < n ? fmaf(p.a, p.x[i], p.y[i]) : 0.f;
     }
   }
 
@@ -138,77 +140,79 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
     float we = __shfl_up_sync(0xFFFFFFFFu, wi, 1);
     if (lane == 0) we = 0.f;
     if (lane < kWarps) s_wexcl[lane] = we;
-    if (lane == kWarps - 1) s_agg = wi;
-  }
-  __syncthreads();
+    // the tile aggregate is the last lane's inclusive value: warp 0 continues straight into the
+    // look-back without another block barrier
+    const float agg = __shfl_sync(0xFFFFFFFFu, wi, kWarps - 1);
 
-  // decoupled look-back across tiles, one warp: each round reads the status words of the 32
-  // nearest unresolved predecessors at once, waits until all are published, then sums back to
-  // the nearest inclusive prefix (positions before tile 0 count as an inclusive prefix of 0)
-  if (warp == 0) {
-    const float agg = s_agg;
+    // decoupled look-back: each round reads the status words of the 32 nearest unresolved
+    // predecessors at once, waits until all are published, then sums back to the nearest
+    // inclusive prefix (positions before tile 0 count as an inclusive prefix of 0)
     if (tile == 0) {
-      if (lane == 0) st_release(&status[0], status_word(epoch, kFlagInc, agg));
-      if (lane == 0) s_prefix = 0.f;
+      if (lane == 0) {
+        st_relaxed(&status[0], status_word(epoch, kFlagInc, agg));
+        s_prefix = 0.f;
+      }
     } else {
-      if (lane == 0) st_release(&status[tile], status_word(epoch, kFlagAgg, agg));
+      if (lane == 0) st_relaxed(&status[tile], status_word(epoch, kFlagAgg, agg));
       float prefix = 0.f;
-      int base = (int)tile - 1;
+      int lb = (int)tile - 1;
       for (;;) {
-        const int j = base - lane;
+        const int j = lb - lane;
         uint32_t flag = kFlagInc;
         float v = 0.f;
         if (j >= 0) {
           int it = 0;
           uint64_t w;
           for (;;) {
-            w = ld_acquire(&status[j]);
+            w = ld_relaxed(&status[j]);
             if ((uint32_t)(w >> 34) == epoch && ((w >> 32) & 3u) != 0) break;
             if (++it > kSpinLimit) {
               atomicOr(&hdr->err, SET_DEVERR_WAIT);
               w = status_word(epoch, kFlagInc, 0.f);
               break;
             }
-            __nanosleep(20);
+            if (it > 16) __nanosleep(20);
           }
           flag = (uint32_t)(w >> 32) & 3u;
           v = __uint_as_float((uint32_t)w);
         }
-        const unsigned inc = __ballot_sync(0xFFFFFFFFu, flag == kFlagInc);
-        const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive prefix in this window
+        const unsigned incm = __ballot_sync(0xFFFFFFFFu, flag == kFlagInc);
+        const int stop = incm ? __ffs(incm) - 1 : 31;  // nearest inclusive prefix in this window
         float t = lane <= stop ? v : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
         prefix += t;
-        if (inc) break;
-        base -= 32;
+        if (incm) break;
+        lb -= 32;
       }
       if (lane == 0) {
-        st_release(&status[tile], status_word(epoch, kFlagInc, prefix + agg));
+        st_relaxed(&status[tile], status_word(epoch, kFlagInc, prefix + agg));
         s_prefix = prefix;
       }
     }
   }
   __syncthreads();
 
-  // S = tile prefix + warp offset + lane offset + thread-serial offset; track max |S|
+  // S = tile prefix + warp offset + lane offset + thread-serial offset; z and S stored together
   const float off = s_prefix + s_wexcl[warp] + lane_excl;
   float mx = 0.f;
   if (vec) {
 #pragma unroll
     for (int q = 0; q < kPer / 4; ++q) {
-      const float4 s = make_float4(off + e[4 * q], off + e[4 * q + 1], off + e[4 * q + 2], off + e[4 * q + 3]);
-      reinterpret_cast<float4*>(p.S + base)[q] = s;
-      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(s.x), fabsf(s.y)), fmaxf(fabsf(s.z), fabsf(s.w))));
+      const float4 sv = make_float4(off + e[4 * q], off + e[4 * q + 1], off + e[4 * q + 2], off + e[4 * q + 3]);
+      reinterpret_cast<float4*>(p.z + base)[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+      reinterpret_cast<float4*>(p.S + base)[q] = sv;
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(sv.x), fabsf(sv.y)), fmaxf(fabsf(sv.z), fabsf(sv.w))));
     }
   } else {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const size_t i = base + k;
       if (i < n) {
-        const float s = off + e[k];
-        p.S[i] = s;
-        mx = fmaxf(mx, fabsf(s));
+        const float sv = off + e[k];
+        p.z[i] = z[k];
+        p.S[i] = sv;
+        mx = fmaxf(mx, fabsf(sv));
       }
     }
   }
@@ -216,39 +220,47 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
   if (lane == 0) s_wmax[warp] = mx;
   __syncthreads();
-  if (tid == 0) {
-    float t = s_wmax[0];
+  if (warp != 0) return;
+  float tm = lane < kWarps ? s_wmax[lane] : 0.f;
 #pragma unroll
-    for (int w = 1; w < kWarps; ++w) t = fmaxf(t, s_wmax[w]);
-    tmax[tile] = t;
-    __threadfence();
-    s_last = atomicAdd(&hdr->done, 1u) == p.T - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
+  for (int o = 16; o > 0; o >>= 1) tm = fmaxf(tm, __shfl_xor_sync(0xFFFFFFFFu, tm, o));
+  if (lane == 0) st_relaxed(&maxw[tile], max_word(epoch, tm));
+  if (tile != p.T - 1) return;
 
-  // last tile: reduce the per-tile maxima, write m and the trailer, reset the scratch
-  __threadfence();
-  if (warp == 0) {
-    float m = 0.f;
-    for (uint32_t t = lane; t < p.T; t += 32) m = fmaxf(m, *reinterpret_cast<volatile float*>(&tmax[t]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-    if (lane == 0) {
-      p.m_out[0] = m;
-      p.m_out[1] = 0.f;
-      p.m_out[2] = 0.f;
-      p.m_out[3] = 0.f;
-      const uint32_t err = *reinterpret_cast<volatile uint32_t*>(&hdr->err);
-      p.trailer->job_id = p.job_id;
-      p.trailer->slot_gen = p.slot_gen;
-      p.trailer->word = trailer_word(err);
-      hdr->err = 0u;
-      hdr->ticket = 0u;
-      hdr->done = 0u;
-      __threadfence();
-      hdr->epoch = (epoch + 1u) & 0x3FFFFFFFu;
+  // last tile: gather every tile's max word (32 per round), write m and the trailer, then
+  // recycle the scratch (new epoch, clear err): every tile has finished its look-back by now
+  const uint64_t tag = (uint64_t)(epoch | 0x80000000u);
+  float m = 0.f;
+  for (uint32_t t0 = 0; t0 < p.T; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    if (t < p.T) {
+      int it = 0;
+      uint64_t w;
+      for (;;) {
+        w = ld_relaxed(&maxw[t]);
+        if ((w >> 32) == tag) break;
+        if (++it > kSpinLimit) {
+          atomicOr(&hdr->err, SET_DEVERR_WAIT);
+          w = 0;
+          break;
+        }
+        if (it > 16) __nanosleep(20);
+      }
+      m = fmaxf(m, __uint_as_float((uint32_t)w));
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if (lane == 0) {
+    p.m_out[0] = m;
+    p.m_out[1] = 0.f;
+    p.m_out[2] = 0.f;
+    p.m_out[3] = 0.f;
+    const uint32_t err = atomicExch(&hdr->err, 0u);
+    p.trailer->job_id = p.job_id;
+    p.trailer->slot_gen = p.slot_gen;
+    p.trailer->word = trailer_word(err);
+    hdr->epoch = (epoch + 1u) & 0x3FFFFFFFu;
   }
 }
 
@@ -289,7 +301,7 @@ bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
 // caching allocator that must not be bypassed), or a latency-critical path where an allocation
 // would synchronise the device.  For them the scan's scratch (header + per-tile status words and
 // maxima) lives in this file-scope device array, sized for n <= kStaticScanMaxN.  Every GPU that
-// loads the library holds it (49,408 bytes) until the process exits.
+// loads the library holds it (65,792 bytes) until the process exits.
 namespace {
 constexpr uint32_t kStaticScanMaxN = 1u << 24;
 constexpr size_t kStaticScanBytes = kScanHdrBytes + (size_t)kScanBytesPerTile * (kStaticScanMaxN / kScanTile);

@@ -18,13 +18,13 @@
 namespace setk {
 
 constexpr int kMaxKernels = 6;
-constexpr size_t kMaxArgBytes = 192;
+constexpr size_t kMaxArgBytes = 512;  // room for two 128-byte TMA descriptors
 
 struct KernelLaunch {
   const void* func = nullptr;
   dim3 grid, block;
   unsigned smem = 0;
-  alignas(16) unsigned char args[kMaxArgBytes];
+  alignas(64) unsigned char args[kMaxArgBytes];
   size_t args_size = 0;
   uint32_t deps = 0;  // bit k: waits for kernel k of the plan; 0 = waits for the H2D copy only
   void* params[1];    // kernel parameter array for launch APIs (points at args)
@@ -51,10 +51,19 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk);
 bool plan_blur_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
+bool plan_mlp_ln(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
+
+// Batched form planners: fill the host table (L.table_bytes) and the kernel launches of one
+// launch over nb jobs whose block starts at d_block.
+bool plan_img_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_t* d_block, uint8_t* h_table,
+                    uint32_t slot_gen, int ctas_per_sm, int tile_variant, KernelLaunch* kl, int* nk);
+bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_t* d_block, uint8_t* h_table,
+                    uint32_t slot_gen, const void* w1, const void* w2, KernelLaunch* kl, int* nk);
 
 // One-time function attributes (dynamic shared memory limits, cluster sizes).
 cudaError_t kernels_init();
 cudaError_t blur_hist_init();
+cudaError_t mlp_init();
 
 template <class A>
 inline void set_args(KernelLaunch& k, const A& a) {

@@ -22,6 +22,7 @@ set_status ctx_less(set_status st, const std::string& msg) {
 
 namespace setrt {
 void set_thread_error(const char* msg) { g_err = msg ? msg : ""; }
+const char* thread_error_text() { return g_err.c_str(); }
 }  // namespace setrt
 
 extern "C" {
@@ -71,6 +72,11 @@ void set_config_default(set_config* c) {
   c->drain_timeout_ms = 30000;
   c->cb_mode = 0;
   c->spin_us = 50;
+  c->cb_every = 1;
+  c->batch_max = 1;
+  c->img_ctas_per_sm = 4;
+  c->img_tile = 0;
+  c->arena_bytes = 0;
 }
 
 set_status set_create_ex(const set_config* cfg, set_ctx** out) {
@@ -129,6 +135,17 @@ set_status set_destroy(set_ctx* ctx) {
 const char* set_last_error(set_ctx* ctx) {
   if (!ctx) return g_err.c_str();
   return ctx->ex->last_error();
+}
+
+set_status set_autotune(set_ctx* ctx, uint32_t type, const set_job_desc* sample, size_t n, set_tune_result* out) {
+  if (!ctx) return ctx_less(SET_EINVAL, "null argument");
+  return ctx->ex->autotune(type, sample, n, out);
+}
+
+set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uint64_t* arrival_ns, size_t n,
+                     set_stats_t* out) {
+  if (!ctx) return ctx_less(SET_EINVAL, "null argument");
+  return ctx->ex->serve(mode, jobs, arrival_ns, n, out);
 }
 
 set_status set_run_baseline(set_ctx* ctx, int kind, const set_job_desc* jobs, size_t n, set_stats_t* out) {

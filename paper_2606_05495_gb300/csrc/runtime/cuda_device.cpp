@@ -9,6 +9,7 @@
 
 #include "../kernels/stages.h"
 #include "executor.h"
+#include "thread_error.h"
 
 namespace setrt {
 namespace {
@@ -23,6 +24,7 @@ namespace {
   } while (0)
 
 constexpr size_t kPlaceholderBytes = 1 << 16;
+constexpr size_t kTableStaging = 96 << 10;  // >= the largest batch table (64 image jobs: 82,176 bytes)
 
 struct GraphInst {
   cudaGraph_t graph = nullptr;
@@ -32,8 +34,22 @@ struct GraphInst {
   int nk = 0;
 };
 
+// Batched form: table H2D, kMaxBatch-capable job copy nodes (unused ones disabled per launch),
+// the packed kernels, and a D2H node per job.
+struct BatchGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t table = nullptr;
+  std::vector<cudaGraphNode_t> h2d, d2h;
+  std::vector<char> on;  // enabled state of job j's copy nodes in the exec
+  cudaGraphNode_t kn[setk::kMaxKernels] = {};
+  int nk = 0;
+};
+
 struct SlotState {
   GraphInst gi[SET_NUM_JOB_TYPES + 1];
+  BatchGraph bg[SET_NUM_JOB_TYPES + 1];
+  uint8_t* h_table = nullptr;  // pinned staging of the batch table (written at dispatch)
   cudaEvent_t done = nullptr;
 };
 
@@ -59,7 +75,8 @@ void template_dims(uint32_t type, uint32_t d[4]) {
 
 void CUDART_CB host_complete(void* p) {
   Slot* s = static_cast<Slot*>(p);
-  s->ex->on_complete(*s, SET_OK);
+  if (s->quiet.load(std::memory_order_acquire)) return;  // a baseline is reusing the slot's graph
+  s->ex->on_complete_group(*s);
 }
 
 cudaKernelNodeParams node_params(setk::KernelLaunch& k) {
@@ -79,16 +96,29 @@ class CudaDevice final : public Device {
   ~CudaDevice() override { release(); }
 
   set_status init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) override;
-  set_status launch(Slot& s, LaunchCost* cost, std::string* err) override;
+  set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override;
+  set_status launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override;
+  set_status autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
+                      std::string* err) override;
+  set_status attach_callback(Slot& s, std::string* err) override;
   void drain() override;
+  uint8_t* arena_base() override { return static_cast<uint8_t*>(arena_); }
+  void thread_init() override {
+    cudaSetDevice(cfg_.device);
+    cudaFree(nullptr);  // the primary context is current on this thread from here on
+  }
   bool supports(uint32_t type) const override {
     return type >= 1 && type <= SET_NUM_JOB_TYPES && supported_[type];
   }
-  set_status run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots, LogHist* lat,
-                          LaunchCost* cost, uint64_t* t0, uint64_t* t1, std::string* err) override;
+  set_status run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots, BuddyArena* arena,
+                          LogHist* lat, LaunchCost* cost, uint64_t* t0, uint64_t* t1, std::string* err) override;
 
  private:
   set_status build_graph(Slot& s, uint32_t type, std::string* err);
+  set_status build_batch_graph(Slot& s, uint32_t type, std::string* err);
+  bool plan_batch(Slot& s, const setk::BatchItem* items, int nb, const setk::BatchLayout& L, uint8_t* d_block,
+                  const void* const shared[2], setk::KernelLaunch* kl, int* nk);
+  uint8_t* batch_block(Slot& s) { return s.job_mem ? s.job_mem : s.dev + ctl_; }
   bool plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::KernelLaunch* kl, int* nk) const;
   set_status update(const Slot& s, const JobRec& j, GraphInst& gi, LaunchCost* cost, std::string* err);
   void release();
@@ -98,19 +128,25 @@ class CudaDevice final : public Device {
   std::vector<SlotState> st_;
   void* pool_ = nullptr;
   bool own_pool_ = false;
+  void* arena_ = nullptr;
   void* ph_host_ = nullptr;
   void* ph_dev_ = nullptr;
   size_t ctl_ = 0;
   bool supported_[SET_NUM_JOB_TYPES + 1] = {};
+  std::atomic<int> img_ctas_{4}, img_tile_{0};  // batched image kernel launch shape (autotuned)
   cudaMemcpyKind kind_in_ = cudaMemcpyHostToDevice, kind_out_ = cudaMemcpyDeviceToHost;
 };
 
 set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) {
   cfg_ = cfg;
+  img_ctas_.store(cfg.img_ctas_per_sm > 0 ? cfg.img_ctas_per_sm : 4);
+  img_tile_.store(cfg.img_tile >= 0 && cfg.img_tile <= 2 ? cfg.img_tile : 0);
   SET_CK(cudaSetDevice(cfg.device));
   SET_CK(cudaFree(nullptr));
   SET_CK(setk::kernels_init());
-  const size_t stride = setk::align256(cfg.slot_bytes);
+  ctl_ = setk::slot_control_bytes(cfg.slot_bytes);
+  // arena mode: slots keep only the kernels' control state; payloads live in the arena
+  const size_t stride = cfg.arena_bytes ? setk::align256(ctl_) : setk::align256(cfg.slot_bytes);
   const size_t need = stride * slots.size();
   if (cfg.pool) {
     if (cfg.pool_bytes < need || (reinterpret_cast<uintptr_t>(cfg.pool) & 255)) {
@@ -128,13 +164,20 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
     own_pool_ = true;
   }
   SET_CK(cudaMemset(pool_, 0, need));  // control blocks start zeroed
+  if (cfg.arena_bytes) {
+    if (cudaMalloc(&arena_, cfg.arena_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      arena_ = nullptr;
+      *err = "cudaMalloc of the arena failed (" + std::to_string(cfg.arena_bytes) + " bytes)";
+      return SET_ENOMEM;
+    }
+  }
   SET_CK(cudaHostAlloc(&ph_host_, kPlaceholderBytes, cudaHostAllocDefault));
   SET_CK(cudaMalloc(&ph_dev_, kPlaceholderBytes));
   if (cfg.io_mode == SET_IO_DEVICE) {
     kind_in_ = cudaMemcpyDeviceToDevice;
     kind_out_ = cudaMemcpyDeviceToDevice;
   }
-  ctl_ = setk::slot_control_bytes(cfg.slot_bytes);
   lanes_.resize(cfg.num_streams);
   cbs_.resize(cfg.num_streams);
   for (int i = 0; i < cfg.num_streams; ++i) {
@@ -144,14 +187,25 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
   st_.resize(slots.size());
   for (auto& s : slots) {
     s.dev = static_cast<uint8_t*>(pool_) + stride * s.index;
-    s.bytes = cfg.slot_bytes;
+    s.bytes = cfg.arena_bytes ? stride : cfg.slot_bytes;
     s.dev_state = &st_[s.index];
     SET_CK(cudaEventCreateWithFlags(&st_[s.index].done, cudaEventDisableTiming));
+    s.job_mem = static_cast<uint8_t*>(arena_);  // templates point into the arena (never launched as built)
     for (uint32_t t = 1; t <= SET_NUM_JOB_TYPES; ++t) {
       if (!(cfg.type_mask & (1u << t))) continue;
       const set_status b = build_graph(s, t, err);
       if (b != SET_OK) return b;
     }
+    if (cfg.batch_max > 1) {
+      SET_CK(cudaHostAlloc(reinterpret_cast<void**>(&st_[s.index].h_table), kTableStaging, cudaHostAllocDefault));
+      std::memset(st_[s.index].h_table, 0, kTableStaging);
+      for (uint32_t t = 1; t <= SET_NUM_JOB_TYPES; ++t) {
+        if (!(cfg.type_mask & (1u << t)) || !setk::batchable(t)) continue;
+        const set_status b = build_batch_graph(s, t, err);
+        if (b != SET_OK) return b;
+      }
+    }
+    s.job_mem = nullptr;
   }
   for (uint32_t t = 1; t <= SET_NUM_JOB_TYPES; ++t) supported_[t] = st_.empty() ? false : st_[0].gi[t].exec != nullptr;
   SET_CK(cudaDeviceSynchronize());
@@ -160,16 +214,17 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
 
 bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::KernelLaunch* kl, int* nk) const {
   if (!setk::job_sizes(j.d.type, j.d.dims, L)) return false;
-  setk::place_job(L, ctl_);
+  uint8_t* base = s.job_mem ? s.job_mem : s.dev;
+  setk::place_job(L, s.job_mem ? 0 : ctl_);
   setk::JobPlanIn in;
   in.type = j.d.type;
   std::memcpy(in.dims, j.d.dims, sizeof in.dims);
   in.scalar = j.d.scalar;
   in.shared[0] = j.d.shared[0];
   in.shared[1] = j.d.shared[1];
-  in.d_in = s.dev + L->in_off;
-  in.d_out = s.dev + L->out_off;
-  in.d_scratch = s.dev + L->scratch_off;
+  in.d_in = base + L->in_off;
+  in.d_out = base + L->out_off;
+  in.d_scratch = base + L->scratch_off;
   in.d_persist = s.dev + setk::control_offset(j.d.type);
   in.job_id = j.id;
   in.slot_gen = s.gen;
@@ -188,12 +243,14 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   setk::KernelLaunch kl[setk::kMaxKernels];
   int nk = 0;
   if (!plan(s, rep, &L, kl, &nk)) return SET_OK;  // type not provided by this build: no graph
-  if (L.end > s.bytes || L.in_bytes > kPlaceholderBytes || L.out_bytes > kPlaceholderBytes) return SET_OK;
+  if ((!s.job_mem && L.end > s.bytes) || L.in_bytes > kPlaceholderBytes || L.out_bytes > kPlaceholderBytes)
+    return SET_OK;
+  uint8_t* base = s.job_mem ? s.job_mem : s.dev;
   GraphInst& gi = st_[s.index].gi[type];
   SET_CK(cudaGraphCreate(&gi.graph, 0));
   const void* src_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
   void* dst_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
-  SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, nullptr, 0, s.dev + L.in_off, src_ph, L.in_bytes, kind_in_));
+  SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, nullptr, 0, base + L.in_off, src_ph, L.in_bytes, kind_in_));
   uint32_t has_dependents = 0;
   for (int k = 0; k < nk; ++k) {
     cudaGraphNode_t deps[setk::kMaxKernels];
@@ -214,7 +271,14 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   size_t ns = 0;
   for (int k = 0; k < nk; ++k)
     if (!(has_dependents & (1u << k))) sinks[ns++] = gi.kn[k];
-  SET_CK(cudaGraphAddMemcpyNode1D(&gi.d2h, gi.graph, sinks, ns, dst_ph, s.dev + L.out_off, L.out_bytes, kind_out_));
+  SET_CK(cudaGraphAddMemcpyNode1D(&gi.d2h, gi.graph, sinks, ns, dst_ph, base + L.out_off, L.out_bytes, kind_out_));
+  if (cfg_.cb_mode == 2) {  // Algorithm 3's callback as the graph's last node, bound to this slot
+    cudaHostNodeParams hp{};
+    hp.fn = host_complete;
+    hp.userData = &s;
+    cudaGraphNode_t hn;
+    SET_CK(cudaGraphAddHostNode(&hn, gi.graph, &gi.d2h, 1, &hp));
+  }
   gi.nk = nk;
   SET_CK(cudaGraphInstantiate(&gi.exec, gi.graph, 0));
   return SET_OK;
@@ -225,19 +289,23 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
   setk::JobLayout L;
   setk::KernelLaunch kl[setk::kMaxKernels];
   int nk = 0;
-  if (!plan(s, j, &L, kl, &nk) || nk != gi.nk) {
-    *err = "job does not match its graph template";
+  setrt::set_thread_error("");
+  const bool planned = plan(s, j, &L, kl, &nk);
+  if (!planned || nk != gi.nk) {
+    *err = std::string("job does not match its graph template (planned=") + (planned ? "1" : "0") +
+           " nk=" + std::to_string(nk) + " template=" + std::to_string(gi.nk) + "): " + setrt::thread_error_text();
     return SET_EINVAL;
   }
+  uint8_t* base = s.job_mem ? s.job_mem : s.dev;
   const uint64_t t0 = now_ns();
-  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, s.dev + L.in_off, j.d.in, L.in_bytes, kind_in_);
+  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
   if (e == cudaSuccess)
     for (int k = 0; k < nk && e == cudaSuccess; ++k) {
       const cudaKernelNodeParams p = node_params(kl[k]);
       e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.kn[k], &p);
     }
   if (e == cudaSuccess)
-    e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.d2h, j.d.out, s.dev + L.out_off, L.out_bytes, kind_out_);
+    e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.d2h, j.d.out, base + L.out_off, L.out_bytes, kind_out_);
   cost->update_ns += now_ns() - t0;
   cost->updates += (uint64_t)nk + 2;
   if (e != cudaSuccess) {
@@ -252,7 +320,20 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
 // LaunchJob (Algorithm 2) + AddCallback: the callback hangs off a per-lane callback stream that
 // waits on an event recorded behind the graph, so the lane stream runs on without a host round
 // trip.
-set_status CudaDevice::launch(Slot& s, LaunchCost* cost, std::string* err) {
+set_status CudaDevice::attach_callback(Slot& s, std::string* err) {
+  SlotState& ss = st_[s.index];
+  cudaStream_t lane = lanes_[s.lane], cb = cbs_[s.lane];
+  if (cfg_.cb_mode == 1) {
+    SET_CK(cudaLaunchHostFunc(lane, host_complete, &s));
+  } else {
+    SET_CK(cudaEventRecord(ss.done, lane));
+    SET_CK(cudaStreamWaitEvent(cb, ss.done, 0));
+    SET_CK(cudaLaunchHostFunc(cb, host_complete, &s));
+  }
+  return SET_OK;
+}
+
+set_status CudaDevice::launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) {
   SlotState& ss = st_[s.index];
   GraphInst& gi = ss.gi[s.job.d.type];
   if (!gi.exec) {
@@ -262,16 +343,267 @@ set_status CudaDevice::launch(Slot& s, LaunchCost* cost, std::string* err) {
   const set_status u = update(s, s.job, gi, cost, err);
   if (u != SET_OK) return u;
   const uint64_t t1 = now_ns();
-  cudaStream_t lane = lanes_[s.lane], cb = cbs_[s.lane];
+  cudaStream_t lane = lanes_[s.lane];
   SET_CK(cudaGraphLaunch(gi.exec, lane));
-  if (cfg_.cb_mode == 1) {
-    SET_CK(cudaLaunchHostFunc(lane, host_complete, &s));
-  } else {
-    SET_CK(cudaEventRecord(ss.done, lane));
-    SET_CK(cudaStreamWaitEvent(cb, ss.done, 0));
-    SET_CK(cudaLaunchHostFunc(cb, host_complete, &s));
+  // cb_mode 2: the graph's own host node runs the completion path
+  if (cfg_.cb_mode != 2 && callback) {
+    const set_status a = attach_callback(s, err);
+    if (a != SET_OK) return a;
   }
   cost->launch_ns += now_ns() - t1;
+  return SET_OK;
+}
+
+bool CudaDevice::plan_batch(Slot& s, const setk::BatchItem* items, int nb, const setk::BatchLayout& L,
+                            uint8_t* d_block, const void* const shared[2], setk::KernelLaunch* kl, int* nk) {
+  SlotState& ss = st_[s.index];
+  if (L.table_bytes > kTableStaging) return false;
+  if (items && nb > 0 && L.nb == nb) {
+    // the type was fixed when the layout was made: image and MLP tables differ in shape
+    if (L.rows) return setk::plan_mlp_batch(items, nb, L, d_block, ss.h_table, s.gen, shared[0], shared[1], kl, nk);
+    return setk::plan_img_batch(items, nb, L, d_block, ss.h_table, s.gen, img_ctas_.load(), img_tile_.load(), kl, nk);
+  }
+  return false;
+}
+
+// Batch graph of one type bound to one slot: table -> {job H2D x kMaxBatch} -> packed kernels ->
+// {job D2H x kMaxBatch}.  Built with placeholders; every launch rebinds the used positions and
+// disables the rest.
+set_status CudaDevice::build_batch_graph(Slot& s, uint32_t type, std::string* err) {
+  SlotState& ss = st_[s.index];
+  BatchGraph& bg = ss.bg[type];
+  setk::BatchItem it{};
+  uint32_t d[4];
+  template_dims(type, d);
+  std::memcpy(it.dims, d, sizeof d);
+  setk::BatchLayout L;
+  if (!setk::batch_layout(type, &it, 1, &L)) return SET_OK;
+  uint8_t* d_block = s.job_mem ? s.job_mem : s.dev + ctl_;
+  if (!s.job_mem && ctl_ + L.block_bytes > s.bytes) return SET_OK;  // slot too small for any batch
+  const void* shared[2] = {ph_dev_, ph_dev_};
+  setk::KernelLaunch kl[setk::kMaxKernels];
+  int nk = 0;
+  if (!plan_batch(s, &it, 1, L, d_block, shared, kl, &nk)) return SET_OK;
+  const int B = cfg_.batch_max;
+  SET_CK(cudaGraphCreate(&bg.graph, 0));
+  SET_CK(cudaGraphAddMemcpyNode1D(&bg.table, bg.graph, nullptr, 0, d_block, ss.h_table, L.table_bytes,
+                                  cudaMemcpyHostToDevice));
+  const void* src_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
+  void* dst_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
+  bg.h2d.assign(B, nullptr);
+  bg.d2h.assign(B, nullptr);
+  bg.on.assign(B, 1);
+  for (int j = 0; j < B; ++j)
+    SET_CK(cudaGraphAddMemcpyNode1D(&bg.h2d[j], bg.graph, nullptr, 0, d_block + L.in_off[0], src_ph, 256, kind_in_));
+  std::vector<cudaGraphNode_t> roots(bg.h2d);
+  roots.push_back(bg.table);
+  uint32_t has_dependents = 0;
+  for (int k = 0; k < nk; ++k) {
+    std::vector<cudaGraphNode_t> deps;
+    if (kl[k].deps == 0) {
+      deps = roots;
+    } else {
+      for (int q = 0; q < k; ++q)
+        if (kl[k].deps & (1u << q)) {
+          deps.push_back(bg.kn[q]);
+          has_dependents |= 1u << q;
+        }
+    }
+    const cudaKernelNodeParams p = node_params(kl[k]);
+    SET_CK(cudaGraphAddKernelNode(&bg.kn[k], bg.graph, deps.data(), deps.size(), &p));
+  }
+  std::vector<cudaGraphNode_t> sinks;
+  for (int k = 0; k < nk; ++k)
+    if (!(has_dependents & (1u << k))) sinks.push_back(bg.kn[k]);
+  for (int j = 0; j < B; ++j)
+    SET_CK(cudaGraphAddMemcpyNode1D(&bg.d2h[j], bg.graph, sinks.data(), sinks.size(), dst_ph, d_block + L.out_off[0],
+                                    256, kind_out_));
+  bg.nk = nk;
+  SET_CK(cudaGraphInstantiate(&bg.exec, bg.graph, 0));
+  return SET_OK;
+}
+
+set_status CudaDevice::launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) {
+  SlotState& ss = st_[s.index];
+  const uint32_t type = s.batch[0].d.type;
+  BatchGraph& bg = ss.bg[type];
+  const int nb = (int)s.batch.size();
+  if (!bg.exec || nb > (int)bg.h2d.size()) {
+    *err = "no batch graph for this job type (batch_max, slot_bytes)";
+    return SET_EINVAL;
+  }
+  setk::BatchItem items[setk::kMaxBatch];
+  for (int j = 0; j < nb; ++j) {
+    std::memcpy(items[j].dims, s.batch[j].d.dims, sizeof items[j].dims);
+    items[j].job_id = s.batch[j].id;
+  }
+  setk::BatchLayout L;
+  uint8_t* d_block = batch_block(s);
+  setk::KernelLaunch kl[setk::kMaxKernels];
+  int nk = 0;
+  const uint64_t t0 = now_ns();
+  if (!setk::batch_layout(type, items, nb, &L) ||
+      !plan_batch(s, items, nb, L, d_block, s.batch[0].d.shared, kl, &nk) || nk != bg.nk) {
+    *err = std::string("batch does not match its graph template: ") + setrt::thread_error_text();
+    return SET_EINVAL;
+  }
+  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(bg.exec, bg.table, d_block, ss.h_table, L.table_bytes,
+                                                     cudaMemcpyHostToDevice);
+  for (int j = 0; j < (int)bg.h2d.size() && e == cudaSuccess; ++j) {
+    const bool use = j < nb;
+    if (use) {
+      const JobRec& jr = s.batch[j];
+      e = cudaGraphExecMemcpyNodeSetParams1D(bg.exec, bg.h2d[j], d_block + L.in_off[j], jr.d.in, L.in_bytes[j], kind_in_);
+      if (e == cudaSuccess)
+        e = cudaGraphExecMemcpyNodeSetParams1D(bg.exec, bg.d2h[j], jr.d.out, d_block + L.out_off[j], L.out_bytes[j],
+                                               kind_out_);
+      cost->updates += 2;
+    }
+    if (e == cudaSuccess && bg.on[j] != (char)use) {
+      e = cudaGraphNodeSetEnabled(bg.exec, bg.h2d[j], use);
+      if (e == cudaSuccess) e = cudaGraphNodeSetEnabled(bg.exec, bg.d2h[j], use);
+      bg.on[j] = (char)use;
+      cost->updates += 2;
+    }
+  }
+  for (int k = 0; k < nk && e == cudaSuccess; ++k) {
+    const cudaKernelNodeParams p = node_params(kl[k]);
+    e = cudaGraphExecKernelNodeSetParams(bg.exec, bg.kn[k], &p);
+    cost->updates += 1;
+  }
+  cost->update_ns += now_ns() - t0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = std::string("batch graph update rejected: ") + cudaGetErrorString(e);
+    return SET_EINVAL;
+  }
+  const uint64_t t1 = now_ns();
+  SET_CK(cudaGraphLaunch(bg.exec, lanes_[s.lane]));
+  if (callback) {
+    const set_status a = attach_callback(s, err);
+    if (a != SET_OK) return a;
+  }
+  cost->launch_ns += now_ns() - t1;
+  return SET_OK;
+}
+
+// Autotuner: every candidate runs the whole sample in batches of B consecutive jobs; per batch the
+// inputs and the table are copied in untimed, and CUDA events bracket the packed kernels only.
+set_status CudaDevice::autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
+                                std::string* err) {
+  if (st_.empty() || !st_[0].h_table) {
+    *err = "autotune needs a context created with batch_max > 1";
+    return SET_EINVAL;
+  }
+  Slot probe;  // a stand-in slot: generation 0, staging of slot 0 (the context is idle)
+  probe.index = 0;
+  std::vector<int> Bs;
+  for (int b = 1; b <= max_batch && b <= (int)n; b *= 2) Bs.push_back(b);
+  std::vector<int> tiles = {0}, ctas = {img_ctas_.load()};
+  if (type == SET_JOB_IMG_SOBEL_HIST) {
+    tiles = {0, 1, 2};
+    ctas = {1, 2, 4, 8};
+  }
+  // scratch block: the largest batch of any candidate
+  size_t need = 0;
+  std::vector<setk::BatchItem> items(n);
+  for (size_t i = 0; i < n; ++i) {
+    std::memcpy(items[i].dims, sample[i].d.dims, sizeof items[i].dims);
+    items[i].job_id = sample[i].id;
+  }
+  for (int B : Bs)
+    for (size_t b0 = 0; b0 < n; b0 += B) {
+      setk::BatchLayout L;
+      if (!setk::batch_layout(type, &items[b0], (int)std::min<size_t>(B, n - b0), &L)) {
+        *err = "autotune: invalid sample";
+        return SET_EINVAL;
+      }
+      need = std::max(need, L.block_bytes);
+    }
+  uint8_t* blk = nullptr;
+  SET_CK(cudaMalloc(&blk, need));
+  cudaStream_t st = lanes_[0];
+  cudaEvent_t e0, e1;
+  SET_CK(cudaEventCreate(&e0));
+  SET_CK(cudaEventCreate(&e1));
+  const int tile0 = img_tile_.load(), cta0 = img_ctas_.load();
+  double best = 0, single = 0;
+  int cands = 0;
+  set_tune_result res{};
+  set_status rs = SET_OK;
+  std::vector<double> by_b(Bs.size(), 0.0);
+  std::vector<set_tune_result> best_of_b(Bs.size());
+  for (size_t bi = 0; bi < Bs.size() && rs == SET_OK; ++bi) {
+    const int B = Bs[bi];
+    for (int tile : tiles)
+      for (int c : ctas) {
+        img_tile_.store(tile);
+        img_ctas_.store(c);
+        double best_ms = 1e30;
+        for (int rep = 0; rep < 2 && rs == SET_OK; ++rep) {
+          double ms_total = 0;
+          for (size_t b0 = 0; b0 < n && rs == SET_OK; b0 += B) {
+            const int nb = (int)std::min<size_t>(B, n - b0);
+            setk::BatchLayout L;
+            setk::batch_layout(type, &items[b0], nb, &L);
+            setk::KernelLaunch kl[setk::kMaxKernels];
+            int nk = 0;
+            if (!plan_batch(probe, &items[b0], nb, L, blk, sample[b0].d.shared, kl, &nk)) {
+              *err = std::string("autotune: plan failed: ") + setrt::thread_error_text();
+              rs = SET_EINVAL;
+              break;
+            }
+            cudaError_t ce = cudaMemcpyAsync(blk, st_[0].h_table, L.table_bytes, cudaMemcpyHostToDevice, st);
+            for (int j = 0; j < nb && ce == cudaSuccess; ++j)
+              ce = cudaMemcpyAsync(blk + L.in_off[j], sample[b0 + j].d.in, L.in_bytes[j], cudaMemcpyDefault, st);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+            for (int k = 0; k < nk && ce == cudaSuccess; ++k)
+              ce = cudaLaunchKernel(kl[k].func, kl[k].grid, kl[k].block, kl[k].params, kl[k].smem, st);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) {
+              *err = std::string("autotune: ") + cudaGetErrorString(ce);
+              rs = SET_ECUDA;
+              break;
+            }
+            ms_total += ms;
+          }
+          best_ms = std::min(best_ms, ms_total);
+        }
+        if (rs != SET_OK) break;
+        ++cands;
+        const double jps = (double)n / (best_ms * 1e-3);
+        if (B == 1) single = std::max(single, jps);
+        if (jps > by_b[bi]) {
+          by_b[bi] = jps;
+          best_of_b[bi].batch_max = B;
+          best_of_b[bi].img_tile = tile;
+          best_of_b[bi].img_ctas_per_sm = c;
+          best_of_b[bi].jobs_per_s = jps;
+        }
+        best = std::max(best, jps);
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(blk);
+  if (rs != SET_OK) {
+    img_tile_.store(tile0);
+    img_ctas_.store(cta0);
+    return rs;
+  }
+  for (size_t bi = 0; bi < Bs.size(); ++bi)  // smallest batch within 5% of the best
+    if (by_b[bi] >= 0.95 * best) {
+      res = best_of_b[bi];
+      break;
+    }
+  res.candidates = cands;
+  res.single_jobs_per_s = single;
+  img_tile_.store(res.img_tile);
+  img_ctas_.store(res.img_ctas_per_sm);
+  *out = res;
   return SET_OK;
 }
 
@@ -287,6 +619,11 @@ void CudaDevice::release() {
       if (gi.exec) cudaGraphExecDestroy(gi.exec);
       if (gi.graph) cudaGraphDestroy(gi.graph);
     }
+    for (auto& bg : ss.bg) {
+      if (bg.exec) cudaGraphExecDestroy(bg.exec);
+      if (bg.graph) cudaGraphDestroy(bg.graph);
+    }
+    if (ss.h_table) cudaFreeHost(ss.h_table);
     if (ss.done) cudaEventDestroy(ss.done);
   }
   st_.clear();
@@ -296,6 +633,8 @@ void CudaDevice::release() {
   cbs_.clear();
   if (own_pool_ && pool_) cudaFree(pool_);
   pool_ = nullptr;
+  if (arena_) cudaFree(arena_);
+  arena_ = nullptr;
   if (ph_host_) cudaFreeHost(ph_host_);
   if (ph_dev_) cudaFree(ph_dev_);
   ph_host_ = ph_dev_ = nullptr;
@@ -304,66 +643,113 @@ void CudaDevice::release() {
 // Baselines of Sec. 5.1.3 on the same kernels and slots.
 //  SET_BASE_SYNC: one stream, one slot; per job cudaMemcpyAsync H2D, plain kernel launches,
 //    cudaMemcpyAsync D2H, stream-ordered, no host synchronisation between jobs.
-//  SET_BASE_BATCH_SYNC: b lanes with one graph exec each (ring entry 0); per batch of b jobs
+//  SET_BASE_BATCH_SYNC: b lanes with one graph exec each (ring entry 0); per batch of up to b jobs
 //    update every exec, launch all, then cudaStreamSynchronize every lane before the next batch.
-set_status CudaDevice::run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots, LogHist* lat,
-                                    LaunchCost* cost, uint64_t* t0, uint64_t* t1, std::string* err) {
+//    With arrival times, a batch holds the jobs that have arrived when it starts (at least one).
+//  In arena mode each lane borrows one arena block sized for the largest job for the whole run.
+set_status CudaDevice::run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots,
+                                    BuddyArena* arena, LogHist* lat, LaunchCost* cost, uint64_t* t0, uint64_t* t1,
+                                    std::string* err) {
   const size_t L = lanes_.size();
+  const size_t nlanes = kind == SET_BASE_SYNC ? 1 : L;
+  size_t need = 0;
+  for (size_t i = 0; i < n; ++i) need = std::max(need, Executor::job_block_bytes(jobs[i].d));
+  std::vector<std::pair<uint8_t*, size_t>> blocks;
+  if (arena) {
+    for (size_t i = 0; i < nlanes; ++i) {
+      size_t bb = 0;
+      uint8_t* p = arena->alloc(need, &bb);
+      if (!p) {
+        for (auto& b : blocks) arena->free(b.first, b.second);
+        *err = "baseline: arena too small for one block per lane";
+        return SET_ENOMEM;
+      }
+      blocks.push_back({p, bb});
+      slots[i].job_mem = p;
+    }
+  }
+  auto release = [&] {
+    for (size_t i = 0; i < blocks.size(); ++i) {
+      slots[i].job_mem = nullptr;
+      arena->free(blocks[i].first, blocks[i].second);
+    }
+  };
+  set_status result = SET_OK;
   if (kind == SET_BASE_SYNC) {
     Slot& s = slots[0];
     cudaStream_t st = lanes_[0];
     *t0 = now_ns();
-    for (size_t i = 0; i < n; ++i) {
+    for (size_t i = 0; i < n && result == SET_OK; ++i) {
       const JobRec& j = jobs[i];
+      while (j.d.t_arrival_ns && now_ns() < j.d.t_arrival_ns) {
+      }
       setk::JobLayout Lo;
       setk::KernelLaunch kl[setk::kMaxKernels];
       int nk = 0;
-      JobRec jj = j;
-      if (!plan(s, jj, &Lo, kl, &nk)) {
+      if (!plan(s, j, &Lo, kl, &nk)) {
         *err = "invalid job";
-        return SET_EINVAL;
+        result = SET_EINVAL;
+        break;
       }
+      uint8_t* base = s.job_mem ? s.job_mem : s.dev;
       const uint64_t ta = now_ns();
-      SET_CK(cudaMemcpyAsync(s.dev + Lo.in_off, j.d.in, Lo.in_bytes, kind_in_, st));
-      for (int k = 0; k < nk; ++k)
-        SET_CK(cudaLaunchKernel(kl[k].func, kl[k].grid, kl[k].block, kl[k].params, kl[k].smem, st));
-      SET_CK(cudaMemcpyAsync(j.d.out, s.dev + Lo.out_off, Lo.out_bytes, kind_out_, st));
+      cudaError_t e = cudaMemcpyAsync(base + Lo.in_off, j.d.in, Lo.in_bytes, kind_in_, st);
+      for (int k = 0; k < nk && e == cudaSuccess; ++k)
+        e = cudaLaunchKernel(kl[k].func, kl[k].grid, kl[k].block, kl[k].params, kl[k].smem, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(j.d.out, base + Lo.out_off, Lo.out_bytes, kind_out_, st);
       cost->launch_ns += now_ns() - ta;
+      if (e != cudaSuccess) {
+        *err = std::string("baseline launch: ") + cudaGetErrorString(e);
+        result = SET_ECUDA;
+      }
       s.gen += 1;
     }
-    SET_CK(cudaStreamSynchronize(st));
+    if (result == SET_OK && cudaStreamSynchronize(st) != cudaSuccess) result = SET_ECUDA;
     *t1 = now_ns();
-    return SET_OK;
+    if (arena) release();
+    return result;
   }
   if (kind == SET_BASE_BATCH_SYNC) {
     *t0 = now_ns();
-    for (size_t base = 0; base < n; base += L) {
-      const size_t nb = std::min(L, n - base);
-      for (size_t i = 0; i < nb; ++i) {
+    size_t base = 0;
+    while (base < n && result == SET_OK) {
+      const uint64_t first = jobs[base].d.t_arrival_ns;
+      while (first && now_ns() < first) {
+      }
+      size_t nb = 1;
+      const uint64_t now = now_ns();
+      while (nb < L && base + nb < n && jobs[base + nb].d.t_arrival_ns <= now) ++nb;
+      for (size_t i = 0; i < nb && result == SET_OK; ++i) {
         Slot& s = slots[i];  // ring entry 0 of lane i
         const JobRec& j = jobs[base + i];
         GraphInst& gi = st_[s.index].gi[j.d.type];
         if (!gi.exec) {
           *err = "job type not instantiated";
-          return SET_EINVAL;
+          result = SET_EINVAL;
+          break;
         }
-        const set_status u = update(s, j, gi, cost, err);
-        if (u != SET_OK) return u;
+        result = update(s, j, gi, cost, err);
+        if (result != SET_OK) break;
         const uint64_t ta = now_ns();
-        SET_CK(cudaGraphLaunch(gi.exec, lanes_[i]));
+        if (cudaGraphLaunch(gi.exec, lanes_[i]) != cudaSuccess) result = SET_ECUDA;
         cost->launch_ns += now_ns() - ta;
       }
-      for (size_t i = 0; i < nb; ++i) SET_CK(cudaStreamSynchronize(lanes_[i]));
+      for (size_t i = 0; i < nb; ++i)
+        if (cudaStreamSynchronize(lanes_[i]) != cudaSuccess) result = SET_ECUDA;
       const uint64_t tb = now_ns();
       for (size_t i = 0; i < nb; ++i) {
         const uint64_t arrival = jobs[base + i].d.t_arrival_ns ? jobs[base + i].d.t_arrival_ns : *t0;
         lat->record(tb > arrival ? tb - arrival : 0);
         slots[i].gen += 1;
       }
+      base += nb;
     }
     *t1 = now_ns();
-    return SET_OK;
+    if (arena) release();
+    if (result == SET_ECUDA && err->empty()) *err = "baseline: CUDA error";
+    return result;
   }
+  if (arena) release();
   *err = "unknown baseline kind";
   return SET_EINVAL;
 }
@@ -383,7 +769,10 @@ extern "C" set_status set_launch_job(const set_job_desc* job, const void* d_in, 
   if ((L.persist_bytes || L.scratch_bytes) && !d_scratch) return SET_EINVAL;
   static thread_local bool inited = false;
   if (!inited) {
-    if (setk::kernels_init() != cudaSuccess) return SET_ECUDA;
+    int dev = 0;  // make the current device's context current on this thread (driver calls need it)
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess || cudaFree(nullptr) != cudaSuccess ||
+        setk::kernels_init() != cudaSuccess)
+      return SET_ECUDA;
     inited = true;
   }
   setk::JobPlanIn in;

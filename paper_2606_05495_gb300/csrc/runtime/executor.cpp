@@ -19,6 +19,9 @@ void normalize(set_config& c) {
   if (c.type_mask == 0) c.type_mask = ~0u;
   if (c.drain_timeout_ms <= 0) c.drain_timeout_ms = 30000;
   if (c.spin_us < 0) c.spin_us = 0;
+  if (c.batch_max < 1) c.batch_max = 1;
+  if (c.batch_max > setk::kMaxBatch) c.batch_max = setk::kMaxBatch;
+  if (c.img_ctas_per_sm < 1) c.img_ctas_per_sm = 4;
 }
 
 // Spins (plain atomic loads, no system call) for up to spin_ns while `ready` is false.
@@ -47,7 +50,7 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
   const uint32_t L = (uint32_t)cfg.num_streams, R = (uint32_t)cfg.ring_depth;
-  ex->slots_.resize((size_t)L * R);
+  ex->slots_ = std::vector<Slot>((size_t)L * R);
   for (uint32_t i = 0; i < L * R; ++i) {
     Slot& s = ex->slots_[i];
     s.index = i;
@@ -62,6 +65,11 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   }
   const set_status st = ex->dev_->init(cfg, ex->slots_, err);
   if (st != SET_OK) return st;
+  if (cfg.arena_bytes) {
+    ex->arena_.init(ex->dev_->arena_base(), cfg.arena_bytes, size_t(64) << 10);
+    ex->use_arena_ = true;
+  }
+  ex->batch_limit_.store(cfg.batch_max);
   for (uint32_t i = 0; i < L; ++i) ex->queues_.emplace_back(new MpmcRing<JobRec>((size_t)cfg.queue_capacity));
   ex->free_.reset(new MpmcRing<uint32_t>((size_t)L * R));
   for (uint32_t i = 0; i < L * R; ++i) ex->free_->push(i);
@@ -118,12 +126,27 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
     return SET_EINVAL;
   }
   const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);
+  if (use_arena_) {
+    if (job_block_bytes(d) > arena_.max_block() || job_block_bytes(d) > cfg_.slot_bytes ||
+        setk::control_offset(d.type) + L.persist_bytes > ctl) {
+      *why = "job larger than the arena's largest block or than slot_bytes";
+      return SET_ENOMEM;
+    }
+    return SET_OK;
+  }
   setk::place_job(&L, ctl);
   if (L.end > cfg_.slot_bytes || setk::control_offset(d.type) + L.persist_bytes > ctl) {
     *why = "job does not fit the slot (slot_bytes too small)";
     return SET_ENOMEM;
   }
   return SET_OK;
+}
+
+size_t Executor::job_block_bytes(const set_job_desc& d) {
+  setk::JobLayout L;
+  if (!setk::job_sizes(d.type, d.dims, &L)) return 0;
+  setk::place_job(&L, 0);
+  return L.end;
 }
 
 // Algorithm 1 (job submitter): claim an id, push to the shortest queue that is not full.
@@ -170,6 +193,7 @@ set_status Executor::submit(const set_job_desc* d, uint64_t* id_out) {
     }
     if (d->flags & SET_F_NONBLOCK) return SET_EAGAIN;
     if (stop_.load()) return SET_ESHUTDOWN;
+    if (spin_until([&] { return space_sig_.load() != seen || stop_.load(); }, (uint64_t)cfg_.spin_us * 1000ull)) continue;
     space_sig_.wait(seen, 50 * 1000000ll);
   }
 }
@@ -206,14 +230,38 @@ bool Executor::find_job(uint32_t lane, JobRec& j, bool& stolen) {
 
 // Algorithm 2, dispatcher loop: pop a free slot (W_pool), FindJob, LaunchJob.  Waiting is a
 // futex sleep on the pool / submit signals, never a poll.
+void Executor::flush_groups(std::vector<Slot*>& pending, std::vector<int>& count) {
+  for (size_t l = 0; l < pending.size(); ++l) {
+    if (!pending[l]) continue;
+    std::string e;
+    const set_status st = dev_->attach_callback(*pending[l], &e);
+    if (st != SET_OK) {
+      fail(st, e);
+      on_complete_group(*pending[l]);  // no callback will come: complete them here (sticky error)
+    }
+    pending[l] = nullptr;
+    count[l] = 0;
+  }
+}
+
 void Executor::worker_main(int) {
+  dev_->thread_init();
   const uint64_t spin_ns = (uint64_t)cfg_.spin_us * 1000ull;
+  const int every = (cfg_.cb_mode == 2 || cfg_.cb_every < 1) ? 1 : cfg_.cb_every;
+  std::vector<Slot*> pending(queues_.size(), nullptr);  // open completion group per lane
+  std::vector<int> count(queues_.size(), 0);
+  JobRec carry;             // batched form: a job popped while filling a batch that did not fit it
+  bool have_carry = false;
   for (;;) {
     uint32_t tok = 0;
     for (;;) {
       const uint32_t seen = free_sig_.load();
-      if (stop_.load()) return;
+      if (stop_.load()) {
+        flush_groups(pending, count);
+        return;
+      }
       if (free_->pop(tok)) break;
+      flush_groups(pending, count);  // about to wait: every launched job must own a callback
       if (spin_until([&] { return free_sig_.load() != seen || stop_.load(); }, spin_ns)) continue;
       free_sig_.wait(seen, -1);
     }
@@ -222,10 +270,17 @@ void Executor::worker_main(int) {
     bool stolen = false, got = false;
     for (;;) {
       const uint32_t seen = job_sig_.load();
+      if (have_carry) {
+        j = carry;
+        have_carry = false;
+        got = true;
+        break;
+      }
       if (find_job(s.lane, j, stolen)) {
         got = true;
         break;
       }
+      flush_groups(pending, count);
       if (stop_.load()) break;
       if (!cfg_.steal) {
         // without stealing, a slot whose lane has no work goes back to the pool so that a
@@ -248,52 +303,147 @@ void Executor::worker_main(int) {
     space_sig_.notify(1);
     if (stolen) steals_.fetch_add(1, std::memory_order_relaxed);
     s.job = j;
+    s.batch.clear();
+    const int blim = batch_limit_.load(std::memory_order_relaxed);
+    if (blim > 1 && setk::batchable(j.d.type)) {
+      // batched form: take what is queued now (no waiting), same type, while it fits one block
+      s.batch.push_back(j);
+      while ((int)s.batch.size() < blim) {
+        JobRec k;
+        bool st2 = false;
+        if (!find_job(s.lane, k, st2)) break;
+        space_sig_.notify(1);
+        if (k.d.type != j.d.type || batch_block_bytes(s.batch, &k) > slot_payload_bytes()) {
+          carry = k;
+          have_carry = true;
+          break;
+        }
+        s.batch.push_back(k);
+      }
+      if (s.batch.size() == 1) s.batch.clear();  // a batch of one runs the single-job graph
+    }
+    if (use_arena_) {
+      // admission by free device memory: wait (in arrival order of this worker) for a block
+      const size_t need = s.batch.empty() ? job_block_bytes(j.d) : batch_block_bytes(s.batch, nullptr);
+      bool waited = false;
+      for (;;) {
+        const uint32_t seen = mem_sig_.load();
+        s.job_mem = arena_.alloc(need, &s.job_mem_bytes);
+        if (s.job_mem || stop_.load()) break;
+        waited = true;
+        if (spin_until([&] { return mem_sig_.load() != seen || stop_.load(); }, spin_ns)) continue;
+        mem_sig_.wait(seen, 100 * 1000000ll);
+      }
+      if (waited) mem_waits_.fetch_add(1, std::memory_order_relaxed);
+      if (!s.job_mem) {
+        on_complete(s, SET_ESHUTDOWN);
+        continue;
+      }
+    }
     if (sticky_.load() != SET_OK) {
       on_complete(s, sticky_.load());
       continue;
     }
     LaunchCost cost;
     std::string e;
-    const set_status st = dev_->launch(s, &cost, &e);
+    s.group_prev = pending[s.lane];
+    const bool close = ++count[s.lane] >= every;
+    const set_status st = s.batch.empty() ? dev_->launch(s, close, &cost, &e) : dev_->launch_batch(s, close, &cost, &e);
+    if (st == SET_OK) {
+      pending[s.lane] = close ? nullptr : &s;
+      if (close) count[s.lane] = 0;
+    } else {
+      count[s.lane] -= 1;
+    }
     updates_.fetch_add(cost.updates, std::memory_order_relaxed);
     update_ns_.fetch_add(cost.update_ns, std::memory_order_relaxed);
     launch_ns_.fetch_add(cost.launch_ns, std::memory_order_relaxed);
     launched_.fetch_add(1, std::memory_order_relaxed);
     if (st != SET_OK) {
       fail(st, e);
+      s.group_prev = nullptr;
       on_complete(s, st);
     }
   }
 }
 
-int32_t Executor::check_trailer(const Slot& s) const {
+void Executor::on_complete_group(Slot& last) {
+  // completing a slot hands it back to W_pool, so read each link before completing its slot
+  Slot* s = &last;
+  while (s) {
+    Slot* prev = s->group_prev;
+    s->group_prev = nullptr;
+    on_complete(*s, SET_OK);
+    s = prev;
+  }
+}
+
+int32_t Executor::check_trailer(const Slot& s, const JobRec& j) const {
   if (cfg_.io_mode != SET_IO_HOST) return SET_OK;
   set_trailer t;
-  std::memcpy(&t, static_cast<const uint8_t*>(s.job.d.out) + s.job.d.out_bytes - sizeof(set_trailer), sizeof t);
-  if (t.job_id != s.job.id || t.slot_gen != s.gen || (t.word >> 16) != SET_TRAILER_MAGIC) return -1000;
+  std::memcpy(&t, static_cast<const uint8_t*>(j.d.out) + j.d.out_bytes - sizeof(set_trailer), sizeof t);
+  if (t.job_id != j.id || t.slot_gen != s.gen || (t.word >> 16) != SET_TRAILER_MAGIC) return -1000;
   if (t.word & 0xFFFFu) return SET_EDEVICE;
   return SET_OK;
 }
 
-// Algorithm 3: ++c_done, return the slot to W_pool, wake one dispatcher.
-void Executor::on_complete(Slot& s, int32_t dev_status) {
+size_t Executor::slot_payload_bytes() const {
+  if (use_arena_) return const_cast<BuddyArena&>(arena_).max_block();
+  const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);
+  return cfg_.slot_bytes > ctl ? cfg_.slot_bytes - ctl : 0;
+}
+
+size_t Executor::batch_block_bytes(const std::vector<JobRec>& b, const JobRec* extra) const {
+  setk::BatchItem items[setk::kMaxBatch];
+  int nb = 0;
+  for (const auto& j : b) {
+    std::memcpy(items[nb].dims, j.d.dims, sizeof items[nb].dims);
+    items[nb++].job_id = j.id;
+  }
+  if (extra) {
+    if (nb >= setk::kMaxBatch) return ~size_t(0);
+    std::memcpy(items[nb].dims, extra->d.dims, sizeof items[nb].dims);
+    items[nb++].job_id = extra->id;
+  }
+  setk::BatchLayout L;
+  if (!setk::batch_layout(b.empty() ? extra->d.type : b[0].d.type, items, nb, &L)) return ~size_t(0);
+  return L.block_bytes;
+}
+
+void Executor::finish_job(Slot& s, const JobRec& j, int32_t dev_status, uint64_t t) {
   int32_t st = dev_status;
   if (st == SET_OK) {
-    st = check_trailer(s);
+    st = check_trailer(s, j);
     if (st == -1000) {
       canary_errors_.fetch_add(1, std::memory_order_relaxed);
       st = SET_EDEVICE;
     }
   }
+  lat_.record(t > j.t_submit_ns ? t - j.t_submit_ns : 0);
+  if (st != SET_OK) c_failed_.fetch_add(1, std::memory_order_relaxed);
+  if (j.d.status) *j.d.status = st;
+}
+
+// Algorithm 3: ++c_done (per job of the slot), return the slot to W_pool, wake one dispatcher.
+void Executor::on_complete(Slot& s, int32_t dev_status) {
   const uint64_t t = now_ns();
-  lat_.record(t - s.job.t_submit_ns);
+  uint64_t n = 1;
+  if (s.batch.empty()) {
+    finish_job(s, s.job, dev_status, t);
+  } else {
+    for (const auto& j : s.batch) finish_job(s, j, dev_status, t);
+    n = s.batch.size();
+  }
   uint64_t last = t_last_ns_.load(std::memory_order_relaxed);
   while (t > last && !t_last_ns_.compare_exchange_weak(last, t)) {
   }
-  if (st != SET_OK) c_failed_.fetch_add(1, std::memory_order_relaxed);
-  if (s.job.d.status) *s.job.d.status = st;
   s.gen += 1;
-  const uint64_t d = c_done_.fetch_add(1) + 1;
+  if (s.job_mem) {
+    arena_.free(s.job_mem, s.job_mem_bytes);
+    s.job_mem = nullptr;
+    mem_sig_.notify(1);
+  }
+  const uint64_t d = c_done_.fetch_add(n) + n;
   free_->push(s.index);  // nothing of `s` is touched after this point
   free_sig_.notify(1);
   if (d >= done_target_.load()) done_sig_.notify_all();
@@ -335,6 +485,8 @@ void Executor::stats(set_stats_t* s) const {
   const uint64_t nl = launched_.load();
   s->mean_update_us = nl ? (double)update_ns_.load() * 1e-3 / (double)nl : 0.0;
   s->mean_launch_us = nl ? (double)launch_ns_.load() * 1e-3 / (double)nl : 0.0;
+  s->mem_waits = mem_waits_.load();
+  s->arena_peak_bytes = use_arena_ ? const_cast<BuddyArena&>(arena_).peak() : 0;
 }
 
 void Executor::reset_stats() {
@@ -347,6 +499,7 @@ void Executor::reset_stats() {
   update_ns_.store(0);
   launch_ns_.store(0);
   launched_.store(0);
+  mem_waits_.store(0);
   t_first_ns_.store(0);
   t_last_ns_.store(0);
   lat_.reset();
@@ -369,7 +522,10 @@ set_status Executor::run_baseline(int kind, const set_job_desc* jobs, size_t n, 
   LaunchCost cost;
   uint64_t t0 = 0, t1 = 0;
   std::string e;
-  const set_status st = dev_->run_baseline(kind, recs.data(), n, slots_, lat, &cost, &t0, &t1, &e);
+  for (auto& s : slots_) s.quiet.store(true);
+  const set_status st =
+      dev_->run_baseline(kind, recs.data(), n, slots_, use_arena_ ? &arena_ : nullptr, lat, &cost, &t0, &t1, &e);
+  for (auto& s : slots_) s.quiet.store(false);
   std::memset(out, 0, sizeof *out);
   if (st == SET_OK) {
     out->submitted = out->completed = n;
@@ -386,6 +542,61 @@ set_status Executor::run_baseline(int kind, const set_job_desc* jobs, size_t n, 
   }
   delete lat;
   return st;
+}
+
+// Request loop of the serving form: arrivals at start + arrival_ns[i].  Under SET the jobs enter
+// through Algorithm 1 as they arrive and overlap with the ones already on the device; under the
+// batch-synchronous baseline the same arrivals are batched by what has arrived.
+set_status Executor::serve(int mode, const set_job_desc* jobs, const uint64_t* arrival_ns, size_t n, set_stats_t* out) {
+  if (!jobs || !arrival_ns || !out || n == 0) return SET_EINVAL;
+  for (size_t i = 1; i < n; ++i)
+    if (arrival_ns[i] < arrival_ns[i - 1]) return fail(SET_EINVAL, "arrival times must be ascending");
+  const set_status w = wait_all(60 * 1000000ll);
+  if (w != SET_OK) return w;
+  const uint64_t t0 = now_ns() + 1000000ull;  // first arrival 1 ms from now
+  if (mode == SET_SERVE_BATCH_SYNC) {
+    std::vector<set_job_desc> d(jobs, jobs + n);
+    for (size_t i = 0; i < n; ++i) d[i].t_arrival_ns = t0 + arrival_ns[i];
+    return run_baseline(SET_BASE_BATCH_SYNC, d.data(), n, out);
+  }
+  if (mode != SET_SERVE_SET) return SET_EINVAL;
+  reset_stats();
+  for (size_t i = 0; i < n; ++i) {
+    const uint64_t target = t0 + arrival_ns[i];
+    while (now_ns() < target) {
+    }
+    set_job_desc d = jobs[i];
+    d.t_arrival_ns = target;
+    d.flags &= ~SET_F_NONBLOCK;
+    const set_status st = submit(&d, nullptr);
+    if (st != SET_OK) return st;
+  }
+  const set_status st = wait_all(600 * 1000000ll);
+  stats(out);
+  if (out->elapsed_s > 0) out->jobs_per_s = (double)out->completed / out->elapsed_s;
+  return st;
+}
+
+set_status Executor::autotune(uint32_t type, const set_job_desc* sample, size_t n, set_tune_result* out) {
+  if (!sample || !out || n == 0 || !setk::batchable(type)) return SET_EINVAL;
+  const set_status w = wait_all(60 * 1000000ll);
+  if (w != SET_OK) return w;
+  std::vector<JobRec> recs(n);
+  std::string why;
+  for (size_t i = 0; i < n; ++i) {
+    if (sample[i].type != type) return fail(SET_EINVAL, "autotune: sample jobs must all have the given type");
+    const set_status v = validate(sample[i], &why);
+    if (v != SET_OK) return fail(v, why);
+    recs[i].d = sample[i];
+    recs[i].id = c_next_.fetch_add(1);
+  }
+  std::string e;
+  for (auto& s : slots_) s.quiet.store(true);
+  const set_status st = dev_->autotune(type, recs.data(), n, cfg_.batch_max, out, &e);
+  for (auto& s : slots_) s.quiet.store(false);
+  if (st != SET_OK) return fail(st, e);
+  batch_limit_.store(out->batch_max);
+  return SET_OK;
 }
 
 }  // namespace setrt

@@ -3,12 +3,14 @@
 // Executor owns queues, the free-slot pool, dispatch threads, counters and the completion path.
 #pragma once
 
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "set.h"
 #include "sync.h"
 
@@ -32,6 +34,11 @@ struct Slot {
   JobRec job{};           // job in flight
   Executor* ex = nullptr;
   void* dev_state = nullptr;  // owned by the Device
+  std::atomic<bool> quiet{false};  // set while a baseline reuses the slot's graphs: no completion path
+  uint8_t* job_mem = nullptr;      // arena mode: the job's [in | out | scratch] block
+  size_t job_mem_bytes = 0;
+  Slot* group_prev = nullptr;      // earlier slot of the same completion group (cb_every > 1)
+  std::vector<JobRec> batch;       // batched form: the jobs of this launch (empty: the single `job`)
 };
 
 struct LaunchCost {
@@ -45,17 +52,31 @@ class Device {
   virtual ~Device() = default;
   // Allocates slot memory and per-slot graph execs; fills dev / bytes / dev_state of every slot.
   virtual set_status init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) = 0;
-  // UpdateGraphParams(job, slot) + GraphLaunch on the slot's lane + AddCallback: the callback,
-  // run after the job's D2H copy, must call Executor::on_complete(slot, device_status).
-  virtual set_status launch(Slot& s, LaunchCost* cost, std::string* err) = 0;
+  // UpdateGraphParams(job, slot) + GraphLaunch on the slot's lane, and AddCallback when
+  // `callback` is set: the callback, run after the D2H copy, must call
+  // Executor::on_complete_group(slot) (the slot and every slot chained through group_prev).
+  virtual set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) = 0;
+  // Batched form: one launch of the slot's batch graph over the jobs in s.batch (same type).
+  virtual set_status launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) = 0;
+  // AddCallback alone: completes the group ending at `s` (already launched) on its lane.
+  virtual set_status attach_callback(Slot& s, std::string* err) = 0;
   // Waits for all device work of the context (used at destruction).
   virtual void drain() = 0;
+  // Called first on every dispatch thread (makes the context's device current on that thread:
+  // driver-API calls such as tensor-map encoding need it before any runtime call has been made).
+  virtual void thread_init() = 0;
+  // Arena mode: device range the executor's buddy allocator manages (nullptr otherwise).
+  virtual uint8_t* arena_base() = 0;
   // True if graphs for jobs of this type were instantiated.
   virtual bool supports(uint32_t type) const = 0;
+  // Autotuner of the batched form (the context's workers are idle): picks jobs per launch (<=
+  // max_batch) and the image kernel's tile / CTAs per SM, applies them to later launches.
+  virtual set_status autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
+                              std::string* err) = 0;
   // Runs a baseline programming model over the same slots (the context's workers are idle).
   virtual set_status run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots,
-                                  LogHist* lat, LaunchCost* cost, uint64_t* t0_ns, uint64_t* t1_ns,
-                                  std::string* err) = 0;
+                                  BuddyArena* arena, LogHist* lat, LaunchCost* cost, uint64_t* t0_ns,
+                                  uint64_t* t1_ns, std::string* err) = 0;
 };
 
 // Product CUDA device; the host-simulation test library links its own factory instead.
@@ -72,22 +93,32 @@ class Executor {
   void stats(set_stats_t* s) const;
   void reset_stats();
   set_status run_baseline(int kind, const set_job_desc* jobs, size_t n, set_stats_t* out);
+  set_status autotune(uint32_t type, const set_job_desc* sample, size_t n, set_tune_result* out);
+  set_status serve(int mode, const set_job_desc* jobs, const uint64_t* arrival_ns, size_t n, set_stats_t* out);
+  // Bytes of the arena block a job needs (its in, out and scratch regions), 0 if invalid.
+  static size_t job_block_bytes(const set_job_desc& d);
   const char* last_error();
 
   // Algorithm 3 (asynchronous resource return).  Runs on the device's callback thread after the
   // slot's D2H copy completed: checks the returned trailer, counts the job done, returns the slot
   // to W_pool and wakes one dispatcher.
   void on_complete(Slot& s, int32_t dev_status);
+  // Completes `last` and every slot chained before it through group_prev (one callback per group).
+  void on_complete_group(Slot& last);
 
   const set_config& config() const { return cfg_; }
 
  private:
   explicit Executor(const set_config& cfg);
   void worker_main(int w);
+  void flush_groups(std::vector<Slot*>& pending, std::vector<int>& count);
   bool find_job(uint32_t lane, JobRec& j, bool& stolen);  // Alg. 2 FindJob
   set_status validate(const set_job_desc& d, std::string* why) const;
   set_status fail(set_status st, const std::string& msg);
-  int32_t check_trailer(const Slot& s) const;
+  int32_t check_trailer(const Slot& s, const JobRec& j) const;
+  void finish_job(Slot& s, const JobRec& j, int32_t dev_status, uint64_t t);
+  size_t batch_block_bytes(const std::vector<JobRec>& b, const JobRec* extra) const;
+  size_t slot_payload_bytes() const;
 
   set_config cfg_;
   std::unique_ptr<Device> dev_;
@@ -109,7 +140,12 @@ class Executor {
   std::atomic<uint64_t> update_ns_{0}, launch_ns_{0}, launched_{0};
   std::atomic<uint64_t> t_first_ns_{0}, t_last_ns_{0};
   std::atomic<uint64_t> stat_base_submitted_{0}, stat_base_done_{0}, stat_base_failed_{0};
+  std::atomic<uint64_t> mem_waits_{0};
   LogHist lat_;
+  BuddyArena arena_;
+  bool use_arena_ = false;
+  std::atomic<int> batch_limit_{1};  // jobs per batched launch (autotuner may lower it)
+  Signal mem_sig_;
 
   std::mutex err_mu_;
   std::string err_;

@@ -45,6 +45,7 @@ bool job_sizes(uint32_t type, const uint32_t d[4], JobLayout* L) {
       // h (bf16, m x F) and LayerNorm(x) (f32, m x D), rows padded to the 128-row GEMM tile
       const size_t mp = (m + 127) & ~size_t(127);
       L->scratch_bytes = align256(mp * kMlpF * 2) + align256(mp * kMlpD * 4);
+      L->persist_bytes = kMlpCtlBytes;
       return true;
     }
     default:
@@ -57,13 +58,74 @@ size_t slot_control_bytes(size_t slot_bytes) {
   return kCtlImgBytes + align256(kScanHdrBytes + kScanBytesPerTile * scan_tiles(slot_bytes / 8 + 1));
 }
 
-size_t control_offset(uint32_t type) { return type == SET_JOB_SAXPY_SCAN_MAX ? kCtlScanOff : kCtlImgOff; }
+size_t control_offset(uint32_t type) {
+  switch (type) {
+    case SET_JOB_SAXPY_SCAN_MAX:
+      return kCtlScanOff;
+    case SET_JOB_MLP_LN:
+      return kCtlMlpOff;
+    default:
+      return kCtlImgOff;
+  }
+}
 
 void place_job(JobLayout* L, size_t ctl) {
   L->in_off = ctl;
   L->out_off = L->in_off + align256(L->in_bytes);
   L->scratch_off = L->out_off + align256(L->out_bytes);
   L->end = L->scratch_off + align256(L->scratch_bytes);
+}
+
+bool batchable(uint32_t type) { return type == SET_JOB_IMG_SOBEL_HIST || type == SET_JOB_MLP_LN; }
+
+// Image batch: table = {header, job descriptors, per-job histogram accumulators}, then each job's
+// input and output region.  MLP batch: table = {control word, per-job trailer records}, then the
+// packed buffers x, h, LayerNorm, out over sum(m_j + 1) rows: job j owns rows [R_j, R_j + m_j)
+// and the spare row R_j + m_j whose first 16 bytes receive its trailer, so that one D2H copy of
+// m_j * 4096 + 16 bytes returns the job's rows and trailer.
+bool batch_layout(uint32_t type, const BatchItem* items, int nb, BatchLayout* L) {
+  if (nb < 1 || nb > kMaxBatch || !batchable(type)) return false;
+  L->nb = nb;
+  size_t off = 0;
+  if (type == SET_JOB_IMG_SOBEL_HIST) {
+    L->table_bytes = align256(kImgHdrBytes + (size_t)nb * (kImgJobDescBytes + kImgJobStateBytes));
+    off = L->table_bytes;
+    for (int j = 0; j < nb; ++j) {
+      JobLayout J;
+      if (!job_sizes(type, items[j].dims, &J)) return false;
+      L->in_off[j] = off;
+      L->in_bytes[j] = J.in_bytes;
+      off += align256(J.in_bytes);
+      L->out_off[j] = off;
+      L->out_bytes[j] = J.out_bytes;
+      off += align256(J.out_bytes);
+    }
+    L->block_bytes = off;
+    return true;
+  }
+  L->table_bytes = align256(kMlpCtlBytes + (size_t)nb * kMlpTrailerRecBytes);
+  size_t rows = 0;
+  size_t R[kMaxBatch];
+  for (int j = 0; j < nb; ++j) {
+    const uint32_t m = items[j].dims[0];
+    if (m < 1 || m > (uint32_t)kMlpMaxM) return false;
+    R[j] = rows;
+    rows += m + 1;
+  }
+  L->rows = rows;
+  const size_t x_off = L->table_bytes;
+  const size_t h_off = x_off + align256(rows * kMlpD * 2);
+  const size_t ln_off = h_off + align256(rows * kMlpF * 2);
+  const size_t o_off = ln_off + align256(rows * kMlpD * 4);
+  L->block_bytes = o_off + align256(rows * kMlpD * 4);
+  for (int j = 0; j < nb; ++j) {
+    const uint32_t m = items[j].dims[0];
+    L->in_off[j] = x_off + R[j] * kMlpD * 2;
+    L->in_bytes[j] = (size_t)m * kMlpD * 2;
+    L->out_off[j] = o_off + R[j] * kMlpD * 4;
+    L->out_bytes[j] = (size_t)m * kMlpD * 4 + sizeof(set_trailer);
+  }
+  return true;
 }
 
 }  // namespace setk

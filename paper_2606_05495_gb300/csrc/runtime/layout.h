@@ -31,4 +31,26 @@ size_t control_offset(uint32_t type);
 // Places the job's regions after a control block of `ctl` bytes.
 void place_job(JobLayout* L, size_t ctl);
 
+// ---- batched form: several jobs of one type in one launch ----
+constexpr int kMaxBatch = 64;
+
+struct BatchItem {
+  uint32_t dims[4];
+  uint64_t job_id;
+};
+
+// One device block per batch: [table | job regions].  The table (job descriptors plus the
+// zero-initialised transient state of the packed kernels) is written on the host and copied in
+// by the batch graph's first node.
+struct BatchLayout {
+  int nb = 0;
+  size_t table_bytes = 0, block_bytes = 0;
+  size_t in_off[kMaxBatch], in_bytes[kMaxBatch], out_off[kMaxBatch], out_bytes[kMaxBatch];
+  size_t rows = 0;  // MLP: packed rows (sum of m_j + 1)
+};
+
+// True for the job types that have a batched form (image, MLP).
+bool batchable(uint32_t type);
+bool batch_layout(uint32_t type, const BatchItem* items, int nb, BatchLayout* L);
+
 }  // namespace setk

@@ -4,4 +4,5 @@
 
 namespace setrt {
 void set_thread_error(const char* msg);
+const char* thread_error_text();
 }  // namespace setrt

@@ -136,3 +136,63 @@ def check_img(job):
         raise AssertionError(f"Sobel image mismatch at {W}x{H}: {len(bad)} px, first {bad[:5].tolist()}")
     assert not o[n:off].any(), "pad bytes not zero"
     assert np.array_equal(o[off:off + 1024].view(np.uint32), h_ref), f"histogram mismatch at {W}x{H}"
+
+
+_WEIGHTS = {}
+
+
+def mlp_weights_dev():
+    """(W1, W2) bf16 device tensors (kept for the session) and their host bit patterns."""
+    if "w" not in _WEIGHTS:
+        t = torch()
+        w1, w2 = datagen.mlp_weights()
+        _WEIGHTS["w"] = (t.from_numpy(w1.view(np.int16)).cuda(), t.from_numpy(w2.view(np.int16)).cuda(), w1, w2)
+    return _WEIGHTS["w"]
+
+
+def mlp_job(j, m=None, **kw):
+    d1, d2, _, _ = mlp_weights_dev()
+    x = datagen.mlp_job(j, m=m)
+    return Job(S().SET_JOB_MLP_LN, (x.shape[0],), x, shared=(d1.data_ptr(), d2.data_ptr()), **kw)
+
+
+MLP_RTOL = 2e-2  # |out - ref| <= 2e-2 * max(|ref|, rms(ref of the job))
+
+
+def check_mlp(job):
+    import oracle
+    _, _, w1, w2 = mlp_weights_dev()
+    m = job.dims[0]
+    ref = oracle.job_mlp_ln(job.payload.reshape(m, 1024), w1, w2)
+    got = job.out()[:m * 4096].view(np.float32).reshape(m, 1024).astype(np.float64)
+    assert np.isfinite(got).all(), "non-finite output"
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    err = np.abs(got - ref)
+    bound = MLP_RTOL * np.maximum(np.abs(ref), rms)
+    worst = float(np.max(err / bound))
+    assert worst <= 1.0, f"m={m}: worst error {worst:.3f} of the bound; max abs err {err.max():.3e}"
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert rel < 1e-2, f"m={m}: norm-wise relative error {rel:.3e}"
+    return rel
+
+
+def serve_jobs(lam, n, img_cap=None):
+    """Jobs and arrival offsets (ns) of a Poisson trace mixing blur / image / MLP jobs 40/40/20.
+    img_cap bounds image sides (keeps the oracle quick in tests)."""
+    t, kinds, ids = datagen.serve_trace(lam, n)
+    jobs = []
+    for kind, j in zip(kinds, ids):
+        if kind == 1:
+            jobs.append(blur_job(int(j)))
+        elif kind == 3:
+            W, H = datagen.img_dims(int(j))
+            if img_cap:
+                W, H = min(W, img_cap), min(H, img_cap)
+            jobs.append(img_job(int(j), dims=(W, H)))
+        else:
+            jobs.append(mlp_job(int(j)))
+    return jobs, (t * 1e9).astype(np.uint64)
+
+
+def check_any(job):
+    {1: check_blur, 2: check_scan, 3: check_img, 4: check_mlp}[job.type](job)

@@ -45,6 +45,9 @@ class SimDevice final : public Device {
     badgen_ = env_long("SET_SIM_BADGEN_EVERY", 0);
     fail_ = env_long("SET_SIM_FAIL_EVERY", 0);
     for (auto& s : slots) s.bytes = cfg.slot_bytes;
+    dropped_.assign(slots.size(), 0);
+    // arena mode: host bytes stand in for the device range (the simulation never touches them)
+    if (cfg.arena_bytes) arena_.resize(cfg.arena_bytes > (64u << 20) ? (64u << 20) : cfg.arena_bytes);
     for (int i = 0; i < cfg.num_streams; ++i) lanes_.emplace_back(new Lane);
     for (int i = 0; i < cfg.num_streams; ++i) lanes_[i]->th = std::thread(&SimDevice::lane_main, this, i);
     cb_th_ = std::thread(&SimDevice::cb_main, this);
@@ -53,19 +56,29 @@ class SimDevice final : public Device {
 
   bool supports(uint32_t type) const override { return type >= 1 && type <= SET_NUM_JOB_TYPES; }
 
-  set_status launch(Slot& s, LaunchCost* cost, std::string* err) override {
+  set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override {
     const uint64_t k = ++launches_;
     cost->updates += 3;
     if (fail_ && k % fail_ == 0) {
       *err = "simulated launch failure";
       return SET_ECUDA;
     }
-    Lane& L = *lanes_[s.lane];
-    {
-      std::lock_guard<std::mutex> g(L.mu);
-      L.q.push_back({&s, k});
-    }
-    L.cv.notify_one();
+    enqueue(&s, k, false);
+    if (callback) enqueue(&s, 0, true);
+    return SET_OK;
+  }
+
+  set_status launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override {
+    return launch(s, callback, cost, err);
+  }
+
+  set_status autotune(uint32_t, const JobRec*, size_t, int, set_tune_result*, std::string* err) override {
+    *err = "the autotuner needs the CUDA device";
+    return SET_EINVAL;
+  }
+
+  set_status attach_callback(Slot& s, std::string*) override {
+    enqueue(&s, 0, true);
     return SET_OK;
   }
 
@@ -85,8 +98,11 @@ class SimDevice final : public Device {
     }
   }
 
-  set_status run_baseline(int, const JobRec*, size_t, std::vector<Slot>&, LogHist*, LaunchCost*, uint64_t*, uint64_t*,
-                          std::string* err) override {
+  uint8_t* arena_base() override { return arena_.data(); }
+  void thread_init() override {}
+
+  set_status run_baseline(int, const JobRec*, size_t, std::vector<Slot>&, BuddyArena*, LogHist*, LaunchCost*,
+                          uint64_t*, uint64_t*, std::string* err) override {
     *err = "baselines need the CUDA device";
     return SET_EINVAL;
   }
@@ -95,7 +111,17 @@ class SimDevice final : public Device {
   struct Item {
     Slot* s;
     uint64_t k;
+    bool cb;  // a completion callback for the group ending at s (runs after earlier items)
   };
+
+  void enqueue(Slot* s, uint64_t k, bool cb) {
+    Lane& L = *lanes_[s->lane];
+    {
+      std::lock_guard<std::mutex> g(L.mu);
+      L.q.push_back({s, k, cb});
+    }
+    L.cv.notify_one();
+  }
   struct Lane {
     std::mutex mu;
     std::condition_variable cv;
@@ -117,18 +143,27 @@ class SimDevice final : public Device {
         L.q.pop_front();
         L.busy = true;
       }
-      const long us = lo_ + (long)(rng() % (uint64_t)(hi_ - lo_ + 1));
-      std::this_thread::sleep_for(std::chrono::microseconds(us));
       Slot& s = *it.s;
-      if (!(drop_ && it.k % drop_ == 0)) {
-        set_trailer t;
-        t.job_id = s.job.id;
-        t.slot_gen = (badgen_ && it.k % badgen_ == 0) ? s.gen + 7 : s.gen;
-        t.word = SET_TRAILER_MAGIC << 16;
-        std::memcpy(static_cast<uint8_t*>(s.job.d.out) + s.job.d.out_bytes - sizeof t, &t, sizeof t);
-        std::lock_guard<std::mutex> g(cb_mu_);
-        cb_q_.push_back(&s);
-        cb_cv_.notify_one();
+      if (it.cb) {
+        // callbacks are the only way slots come back; a dropped one strands its whole group
+        if (!dropped_[s.index]) {
+          std::lock_guard<std::mutex> g(cb_mu_);
+          cb_q_.push_back(&s);
+          cb_cv_.notify_one();
+        }
+      } else {
+        const long us = lo_ + (long)(rng() % (uint64_t)(hi_ - lo_ + 1));
+        std::this_thread::sleep_for(std::chrono::microseconds(us));
+        auto write = [&](const JobRec& j) {
+          set_trailer t;
+          t.job_id = j.id;
+          t.slot_gen = (badgen_ && it.k % badgen_ == 0) ? s.gen + 7 : s.gen;
+          t.word = SET_TRAILER_MAGIC << 16;
+          std::memcpy(static_cast<uint8_t*>(j.d.out) + j.d.out_bytes - sizeof t, &t, sizeof t);
+        };
+        if (s.batch.empty()) write(s.job);
+        for (const auto& j : s.batch) write(j);
+        dropped_[s.index] = drop_ && it.k % drop_ == 0;
       }
       std::lock_guard<std::mutex> g(L.mu);
       L.busy = false;
@@ -146,7 +181,7 @@ class SimDevice final : public Device {
         cb_q_.pop_front();
         cb_busy_ = true;
       }
-      s->ex->on_complete(*s, SET_OK);
+      s->ex->on_complete_group(*s);
       std::lock_guard<std::mutex> g(cb_mu_);
       cb_busy_ = false;
     }
@@ -170,6 +205,8 @@ class SimDevice final : public Device {
   }
 
   long lo_ = 5, hi_ = 50, drop_ = 0, badgen_ = 0, fail_ = 0;
+  std::vector<uint8_t> arena_;
+  std::vector<char> dropped_;  // per slot: its last job "lost" its callback
   std::atomic<uint64_t> launches_{0};
   std::vector<std::unique_ptr<Lane>> lanes_;
   std::mutex cb_mu_;

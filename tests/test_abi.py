@@ -35,6 +35,8 @@ STRUCTS = {
     "set_config": S.set_config,
     "set_stats_t": S.set_stats_t,
     "set_trailer": S.set_trailer,
+    "set_trace_summary": S.set_trace_summary,
+    "set_tune_result": S.set_tune_result,
 }
 
 
@@ -72,7 +74,7 @@ def test_documented_payload_sizes():
     for t, dims in [(1, d(0, 5)), (1, d(2049, 5)), (2, d(0)), (2, d(1 << 27)), (3, d(4097, 2)), (4, d(0)),
                     (4, d(257)), (9, d(1, 1))]:
         assert S.set_job_in_bytes(t, dims) == 0 and S.set_job_out_bytes(t, dims) == 0
-    assert S.set_job_scratch_bytes(2, d(65536)) == 256  # 64-byte header + 16 tiles x 12 bytes, aligned
+    assert S.set_job_scratch_bytes(2, d(65536)) == 512  # 64-byte header + 16 tiles x 16 bytes, aligned
     sb = S.set_job_slot_bytes(2, d(65536))
     assert sb >= 2 * 524288 and sb < 2 * 524288 + 4096
 

@@ -98,3 +98,28 @@ def test_baselines_compute_the_same_results(kind):
         s.set_destroy(ctx)
     for j in jobs:
         (check_blur if j.type == s.SET_JOB_BLUR_HIST else check_scan)(j)
+
+
+@pytest.mark.parametrize("cb_mode", [0, 1, 2])
+def test_callback_modes_and_baseline_reuse(cb_mode):
+    s = S()
+    jobs = [scan_job(k, n=20000 + k) for k in range(120)]
+    ctx = s.create(s.default_config(num_streams=4, num_workers=1, slot_bytes=1 << 20, cb_mode=cb_mode))
+    try:
+        # a baseline first: it reuses the slots' graphs, whose completion path must stay quiet
+        arr = (s.set_job_desc * 8)(*[j.desc for j in jobs[:8]])
+        st = s.set_stats_t()
+        s.check(s.set_run_baseline(ctx, s.SET_BASE_BATCH_SYNC, arr, 8, ctypes.byref(st)), "baseline", ctx)
+        arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+        first = ctypes.c_uint64()
+        s.check(s.set_submit_many(ctx, arr, len(jobs), ctypes.byref(first), None), "submit", ctx)
+        s.check(s.set_wait_all(ctx, 60_000_000), "wait", ctx)
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "stats", ctx)
+        assert st.completed == len(jobs) and st.failed == 0 and st.canary_errors == 0
+        for k, j in enumerate(jobs):
+            j.id = first.value + k
+    finally:
+        s.set_destroy(ctx)
+    for j in jobs:
+        check_scan(j)
+    check_trailers(jobs)

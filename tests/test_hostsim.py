@@ -40,19 +40,20 @@ def sim():
 
 
 class Jobs:
-    """n tiny blur jobs (16x16) with host in/out buffers; the simulation writes only trailers."""
+    """n tiny blur (or image) jobs, 16x16, with host in/out buffers; the simulation writes only
+    trailers."""
 
-    def __init__(self, n, flags=0):
+    def __init__(self, n, flags=0, type_=1):
         self.dims = B.dims4(16, 16)
-        self.inb = np.zeros(256, np.uint8)
-        ob = B.set_job_out_bytes(1, self.dims)
+        self.inb = np.zeros(3 * 256, np.uint8)
+        ob = B.set_job_out_bytes(type_, self.dims)
         self.out = np.zeros((n, ob), np.uint8)
         self.status = (ctypes.c_int32 * n)(*([99] * n))
         self.descs = (B.set_job_desc * n)()
         for k in range(n):
             d = self.descs[k]
-            d.type, d.flags, d.dims = 1, flags, self.dims
-            d.in_, d.in_bytes = self.inb.ctypes.data, 256
+            d.type, d.flags, d.dims = type_, flags, self.dims
+            d.in_, d.in_bytes = self.inb.ctypes.data, B.set_job_in_bytes(type_, self.dims)
             d.out, d.out_bytes = self.out[k].ctypes.data, ob
             d.status = ctypes.cast(ctypes.byref(self.status, 4 * k), ctypes.POINTER(ctypes.c_int32))
 
@@ -98,6 +99,37 @@ def test_every_job_completes_exactly_once(sim):
     assert all(s == 0 for s in jobs.status)
     assert st.p50_us <= st.p99_us <= st.max_us * 1.02 + 1
     assert st.steals > 0  # with uneven delays some lane always runs dry first
+
+
+@pytest.mark.parametrize("every,lanes,ring", [(2, 3, 2), (4, 2, 1), (8, 5, 3), (3, 1, 1)])
+def test_completion_groups_never_strand_slots(sim, every, lanes, ring):
+    os.environ["SET_SIM_DELAY_US"] = "1,30"
+    n = 700
+    jobs = Jobs(n)
+    ctx = create(sim, num_streams=lanes, num_workers=1, ring_depth=ring, cb_every=every)
+    rc, first, done = submit_all(sim, ctx, jobs, n)
+    assert rc == 0 and done == n
+    assert sim.set_wait_all(ctx, 30_000_000) == 0
+    st = stats(sim, ctx)
+    sim.set_destroy(ctx)
+    assert st.completed == n and st.failed == 0 and st.canary_errors == 0
+    assert np.array_equal(np.sort(jobs.trailer_ids()), np.arange(first, first + n, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("batch_max,every", [(4, 1), (8, 3), (64, 2)])
+def test_batches_complete_every_job_once(sim, batch_max, every):
+    os.environ["SET_SIM_DELAY_US"] = "5,60"
+    n = 900
+    jobs = Jobs(n, type_=3)
+    ctx = create(sim, num_streams=3, num_workers=1, ring_depth=2, batch_max=batch_max, cb_every=every,
+                 slot_bytes=1 << 20)
+    rc, first, done = submit_all(sim, ctx, jobs, n)
+    assert rc == 0 and done == n
+    assert sim.set_wait_all(ctx, 30_000_000) == 0
+    st = stats(sim, ctx)
+    sim.set_destroy(ctx)
+    assert st.completed == n and st.failed == 0 and st.canary_errors == 0
+    assert np.array_equal(np.sort(jobs.trailer_ids()), np.arange(first, first + n, dtype=np.uint64))
 
 
 def test_no_steal_mode_keeps_jobs_on_their_lane(sim):
@@ -196,5 +228,6 @@ def test_sanitizer_stress(san):
                SET_SIM_DELAY_US="0,20")
     for k in ("SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY"):
         env.pop(k, None)
-    r = subprocess.run([exe, "6000"], capture_output=True, text=True, env=env, timeout=600)
-    assert r.returncode == 0, r.stdout + r.stderr[-3000:]
+    for every in ("1", "3"):
+        r = subprocess.run([exe, "6000", every], capture_output=True, text=True, env=env, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr[-3000:]
