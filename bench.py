@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
+    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve"], default="scan",
+                   help="scan (default) is the headline line; the others measure the other workloads")
+    p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
     return p.parse_args()
 
 
@@ -434,12 +437,183 @@ def run_set(args, d: Dist):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- the other workloads
+
+class JobSet:
+    """Jobs of one kind with inputs / outputs in two pinned buffers (and device copies)."""
+
+    def __init__(self, S, kind, ids, dims=None, device_copy=False):
+        import numpy as np
+
+        import datagen
+        t = _torch()
+        self.kind, self.ids = kind, list(ids)
+        self.dims = []
+        for k, j in enumerate(self.ids):
+            if kind == 1:
+                self.dims.append((256, 256))
+            elif kind == 3:
+                self.dims.append(dims[k] if dims else datagen.img_dims(j))
+            else:
+                self.dims.append((dims[k] if dims else datagen.mlp_rows(j),))
+        ib = [S.set_job_in_bytes(kind, S.dims4(*d)) for d in self.dims]
+        ob = [S.set_job_out_bytes(kind, S.dims4(*d)) for d in self.dims]
+        self.in_off = np.concatenate([[0], np.cumsum([(b + 255) // 256 * 256 for b in ib])]).astype(np.int64)
+        self.out_off = np.concatenate([[0], np.cumsum([(b + 255) // 256 * 256 for b in ob])]).astype(np.int64)
+        self.h_in = t.empty(int(self.in_off[-1]), dtype=t.uint8, pin_memory=True)
+        self.h_out = t.zeros(int(self.out_off[-1]), dtype=t.uint8, pin_memory=True)
+        hv = self.h_in.numpy()
+        for k, j in enumerate(self.ids):
+            seg = hv[self.in_off[k]:self.in_off[k] + ib[k]]
+            if kind == 1:
+                datagen.blur_job(j, out=seg)
+            elif kind == 3:
+                datagen.img_job(j, out=seg, dims=self.dims[k])
+            else:
+                datagen.mlp_job(j, out=seg.view(np.uint16), m=self.dims[k][0])
+        self.shared = (None, None)
+        if kind == 4:
+            w1, w2 = datagen.mlp_weights()
+            self.w = (t.from_numpy(w1.view(np.int16)).cuda(), t.from_numpy(w2.view(np.int16)).cuda())
+            self.shared = (self.w[0].data_ptr(), self.w[1].data_ptr())
+        self.bytes_in, self.bytes_out = sum(ib), sum(ob)
+        self.descs = self._descs(S, self.h_in.data_ptr(), self.h_out.data_ptr())
+        if device_copy:
+            self.d_in = self.h_in.cuda()
+            self.d_out = t.zeros_like(self.h_out, device="cuda")
+            self.descs_dev = self._descs(S, self.d_in.data_ptr(), self.d_out.data_ptr())
+
+    def _descs(self, S, ib, ob):
+        arr = (S.set_job_desc * len(self.ids))()
+        for k in range(len(self.ids)):
+            arr[k] = S.make_desc(self.kind, self.dims[k], ib + int(self.in_off[k]), ob + int(self.out_off[k]),
+                                 shared=self.shared)
+        return arr
+
+    def slot_bytes(self, S):
+        return max(S.set_job_slot_bytes(self.kind, S.dims4(*d)) for d in self.dims)
+
+    def rows(self):
+        return sum(d[0] for d in self.dims)
+
+
+def _rate(S, cfg, descs, n, args, d):
+    """jobs/s of the SET executor over `steps` timed steps, with the stats of those steps."""
+    ctx = S.create(S.default_config(**cfg))
+    try:
+        ms, st = timed(S, ctx, descs, n, args, d)
+        return {"jobs_per_s": n / (ms * 1e-3), "ms_per_step": ms, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                "failed": st["failed"], "canary_errors": st["canary_errors"]}
+    finally:
+        S.set_destroy(ctx)
+
+
+def _baseline(S, cfg, kind, descs, n):
+    ctx = S.create(S.default_config(**cfg))
+    try:
+        st = S.set_stats_t()
+        S.check(S.set_run_baseline(ctx, kind, descs, n, ctypes.byref(st)), "baseline", ctx)
+        S.check(S.set_run_baseline(ctx, kind, descs, n, ctypes.byref(st)), "baseline", ctx)
+        return {"jobs_per_s": st.jobs_per_s, "p50_us": st.p50_us, "p99_us": st.p99_us}
+    finally:
+        S.set_destroy(ctx)
+
+
+def run_workload(args, d: Dist):
+    """One JSON line per workload: SET forms against the batch-synchronous graph baseline."""
+    import paper_2606_05495_gb300 as S
+    t = _torch()
+    t.cuda.set_device(d.local)
+    line = {"workload": args.workload, "unit": "jobs/s", "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic (seeded SplitMix64 inputs)"}
+    common = dict(num_workers=1, cb_mode=0, device=d.local)
+    if args.workload == "blur":
+        # 64 jobs of 64 KiB last tens of microseconds: a step runs the 64-job configuration 200 times
+        # over (12,800 distinct jobs, each with its own input and output)
+        n = 64 * 200
+        js = JobSet(S, 1, range(n), device_copy=True)
+        cfg = dict(common, num_streams=2, ring_depth=4, slot_bytes=js.slot_bytes(S))
+        line["config"] = {"jobs_per_step": n, "side": 256, "streams": 2, "note": "64-job configuration x 200"}
+        line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d)
+        line["set_per_job_callbacks"] = _rate(S, dict(cfg, cb_every=1), js.descs, n, args, d)
+        line["set_device_resident"] = _rate(S, dict(cfg, cb_every=8, io_mode=S.SET_IO_DEVICE), js.descs_dev, n, args, d)
+        line["set_16_streams"] = _rate(S, dict(cfg, cb_every=8, num_streams=16), js.descs, n, args, d)
+        line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
+        line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
+    elif args.workload in ("img", "mlp"):
+        kind = 3 if args.workload == "img" else 4
+        n = min(args.jobs, 2000)
+        js = JobSet(S, kind, range(n))
+        sb = js.slot_bytes(S)
+        cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=sb)
+        line["config"] = {"jobs": n, "sample_of": 10000 if kind == 3 else 2000, "streams": 16,
+                          "in_bytes": js.bytes_in, "out_bytes": js.bytes_out}
+        line["set_per_job"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d)
+        if kind == 3:
+            line["set_per_stage_graphs"] = _rate(S, dict(cfg, cb_every=8, img_fused=0), js.descs, n, args, d)
+        # batched form: autotuned jobs per launch (and tile / CTAs per SM for images) in an 8 GiB arena
+        bcfg = dict(cfg, cb_every=2, ring_depth=2, batch_max=16, arena_bytes=8 << 30, slot_bytes=1 << 30)
+        ctx = S.create(S.default_config(**bcfg))
+        tune = S.set_tune_result()
+        ns = min(n, 64)
+        S.check(S.set_autotune(ctx, kind, js.descs, ns, ctypes.byref(tune)), "set_autotune", ctx)
+        ms, st = timed(S, ctx, js.descs, n, args, d)
+        S.set_destroy(ctx)
+        line["set_batched"] = {"jobs_per_s": n / (ms * 1e-3), "ms_per_step": ms, "p99_us": st["p99_us"],
+                               "failed": st["failed"], "autotune": tune.as_dict()}
+        line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
+        if kind == 4:
+            flop = 2.0 * js.rows() * 1024 * 4096 * 2
+            line["gemm_tflops_e2e"] = {k: flop / (line[k]["ms_per_step"] * 1e-3) / 1e12
+                                       for k in ("set_per_job", "set_batched")}
+    elif args.workload == "serve":
+        import numpy as np
+
+        import datagen
+        npool = args.jobs if args.jobs != 4096 else 2000
+        rates = [float(r) for r in args.rates.split(",")]
+        pools = {}
+        for lam in rates[:1]:
+            _, kinds, _ = datagen.serve_trace(lam, npool)
+        counts = {k: int((kinds == k).sum() * 1.15) + 16 for k in (1, 3, 4)}  # traces of other rates vary
+        for k in (1, 3, 4):
+            pools[k] = JobSet(S, k, range(50000 + 100000 * k, 50000 + 100000 * k + counts[k]))
+        cfg = dict(common, num_streams=16, ring_depth=4, cb_every=1, slot_bytes=64 << 20, arena_bytes=8 << 30)
+        cfg["cb_mode"] = 1  # host function on the lane stream: one hop less on the completion path
+        line["config"] = {"arrivals_per_rate": npool, "mix": "40% blur 256x256, 40% image (log-uniform sides), "
+                          "20% MLP (m 1..256)", "arena_bytes": 8 << 30, "streams": 16}
+        sweep = []
+        for lam in rates:
+            ts, kinds, _ = datagen.serve_trace(lam, npool)
+            used = {1: 0, 3: 0, 4: 0}
+            arr = (S.set_job_desc * npool)()
+            for i, k in enumerate(kinds):
+                arr[i] = pools[int(k)].descs[used[int(k)] % len(pools[int(k)].ids)]
+                used[int(k)] += 1
+            off = (ctypes.c_uint64 * npool)(*[int(x * 1e9) for x in ts])
+            row = {"rate": lam}
+            for name, mode in (("set", S.SET_SERVE_SET), ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC)):
+                ctx = S.create(S.default_config(**cfg))
+                st = S.set_stats_t()
+                S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)
+                S.set_destroy(ctx)
+                row[name] = {"jobs_per_s": st.jobs_per_s, "p50_us": st.p50_us, "p99_us": st.p99_us,
+                             "failed": st.failed, "mem_waits": st.mem_waits}
+            sweep.append(row)
+            print(json.dumps(row), flush=True)
+        line["sweep"] = sweep
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     d = Dist()
     try:
         if args.impl == "reference":
             run_reference(args, d)
+        elif args.workload != "scan":
+            run_workload(args, d)
         else:
             run_set(args, d)
     finally:

@@ -143,6 +143,10 @@ typedef struct {
                           MLP) share one launch of packed persistent kernels (default 1 = off) */
   int img_ctas_per_sm; /* batched image kernel: persistent CTAs per SM (default 4) */
   int img_tile;        /* batched image kernel tile: 0 = 32x128 (default), 1 = 16x256, 2 = 64x64 */
+  int stamps;          /* 1: stage kernels write entry / exit tickets of one device counter and the
+                          completion path checks every DAG edge (exit of a stage before entry of
+                          its successor); violations count in set_stats_t.order_errors (test
+                          invariant, default 0) */
   size_t arena_bytes;  /* serving form: 0 (default) = every job uses its slot's memory; > 0 = each
                           job's in/out/scratch is allocated at dispatch from a device arena of this
                           size (buddy blocks, 64 KiB minimum) and freed by its completion callback,
@@ -161,6 +165,7 @@ typedef struct {
   double mean_update_us;    /* host time of UpdateGraphParams per job */
   double mean_launch_us;    /* host time of graph launch + callback chaining per job */
   uint64_t mem_waits;       /* arena mode: dispatches that waited for free memory */
+  uint64_t order_errors;    /* stamps mode: jobs whose stage order was violated (should be 0) */
   uint64_t arena_peak_bytes;/* arena mode: peak bytes allocated */
 } set_stats_t;
 

@@ -47,7 +47,7 @@ class set_config(ctypes.Structure):
                 ("queue_capacity", c_int), ("steal", c_int), ("io_mode", c_int), ("img_fused", c_int),
                 ("pool", c_void_p), ("pool_bytes", c_size_t), ("type_mask", c_uint32), ("device", c_int),
                 ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int), ("cb_every", c_int),
-                ("batch_max", c_int), ("img_ctas_per_sm", c_int), ("img_tile", c_int),
+                ("batch_max", c_int), ("img_ctas_per_sm", c_int), ("img_tile", c_int), ("stamps", c_int),
                 ("arena_bytes", c_size_t)]
 
 
@@ -56,7 +56,7 @@ class set_stats_t(ctypes.Structure):
                 ("updates", c_uint64), ("canary_errors", c_uint64), ("elapsed_s", c_double),
                 ("jobs_per_s", c_double), ("p50_us", c_double), ("p99_us", c_double), ("max_us", c_double),
                 ("mean_update_us", c_double), ("mean_launch_us", c_double), ("mem_waits", c_uint64),
-                ("arena_peak_bytes", c_uint64)]
+                ("order_errors", c_uint64), ("arena_peak_bytes", c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -22,6 +22,7 @@ constexpr int kChunkRows = 32;
 constexpr int kMaxW = kBlurMaxW;
 
 struct BlurHistArgs {
+  Stamp stamp;  // first member: filled by the planner
   const uint8_t* in;
   uint8_t* out;
   uint8_t* pad;  // zero bytes between image and histogram
@@ -37,6 +38,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
   extern __shared__ __align__(16) uint8_t tile[];  // (kChunkRows + 2) rows x pitch
   __shared__ uint32_t whist[kWarps][256];
   __shared__ uint32_t chist[256];
+  stamp_entry(a.stamp);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -124,6 +126,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
     a.trailer->word = trailer_word(0);
   }
   cluster.sync();  // every CTA's chist stays alive until the remote reads are done
+  stamp_exit(a.stamp);
 }
 
 inline size_t blur_img_bytes(const uint32_t d[4]) { return (size_t)d[0] * d[1]; }

@@ -48,7 +48,7 @@ struct ImgJobDev {
   uint32_t item0, nitems;  // first global work item of this job, number of items
   uint32_t chunks;         // column chunks per band
   uint32_t slot_gen, npad;
-  uint32_t pad_;
+  uint32_t chunk_cols;     // columns of one work item (a multiple of the tile width)
 };
 
 static_assert(sizeof(ImgJobDev) <= kImgJobDescBytes, "job descriptor fits its table stride");
@@ -60,6 +60,7 @@ struct ImgHdr {
 static_assert(sizeof(ImgHdr) == kImgHdrBytes, "image header size shared with the layout code");
 
 struct ImgFusedArgs {
+  Stamp stamp;  // first member: filled by the planner
   const ImgJobDev* table;  // device table of njobs entries, or nullptr: use `one`
   ImgHdr* hdr;
   uint32_t njobs, total_items;
@@ -67,17 +68,20 @@ struct ImgFusedArgs {
 };
 
 struct SobelHistArgs {
+  Stamp stamp;  // first member: filled by the planner
   ImgFusedArgs a;
   const uint8_t* q;  // Gaussian image
 };
 
 struct GrayArgs {
+  Stamp stamp;  // first member: filled by the planner
   const uint8_t* rgb;
   uint8_t* gray;
   size_t px;
 };
 
 struct GaussArgs {
+  Stamp stamp;  // first member: filled by the planner
   const uint8_t* g;
   uint8_t* q;
   uint32_t W, H;
@@ -94,6 +98,45 @@ __device__ void stage_gray(uint8_t (*g_s)[P], const uint8_t* __restrict__ rgb, i
     const int r = i / GC, c = i - r * GC;
     const uint8_t* p = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + clampi(x0 + c, W));
     g_s[r][c] = (uint8_t)gray_of(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+  }
+}
+
+// stage_gray for a tile whose staged columns [x0, x0 + GC) lie inside the image: every staged row
+// is one contiguous run of 3 * GC bytes, fetched with aligned 4-byte loads into raw_s (the run
+// starts `lead` bytes into its first word), then converted from shared memory.  Rows are
+// clamped as before.  A run is only read up to its own last word, which never passes the end of
+// the image except on the image's last row; that row is fetched bytewise.
+template <int GR, int GC, int P, int RAW>
+__device__ void stage_gray_rows(uint8_t (*g_s)[P], uint32_t (*raw_s)[RAW], const uint8_t* __restrict__ rgb, int W,
+                                int H, int y0, int x0) {
+  constexpr int kBytes = 3 * GC;
+  static_assert(RAW * 4 >= kBytes + 3 + 4, "raw row holds the run and its alignment slack");
+  for (int i = threadIdx.x; i < GR * RAW; i += kThreads) {
+    const int r = i / RAW, w = i - r * RAW;
+    const int Y = clampi(y0 + r, H);
+    const uint8_t* run = rgb + 3 * ((size_t)Y * W + x0);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(run) & ~uintptr_t(3);
+    const int lead = (int)(reinterpret_cast<uintptr_t>(run) - a0);
+    const int nwords = (lead + kBytes + 3) >> 2;
+    if (w >= nwords) continue;
+    if (Y == H - 1) {  // last image row: never read past the image's last byte
+      uint32_t v = 0;
+      for (int b = 0; b < 4; ++b) {
+        const intptr_t off = (intptr_t)(4 * w + b) - lead;
+        if (off >= 0 && off < kBytes) v |= (uint32_t)__ldg(run + off) << (8 * b);
+      }
+      raw_s[r][w] = v;
+    } else {
+      raw_s[r][w] = __ldg(reinterpret_cast<const uint32_t*>(a0) + w);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < GR * GC; i += kThreads) {
+    const int r = i / GC, c = i - r * GC;
+    const uint8_t* run = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + x0);
+    const int lead = (int)(reinterpret_cast<uintptr_t>(run) & 3);
+    const uint8_t* b = reinterpret_cast<const uint8_t*>(raw_s[r]) + lead + 3 * c;
+    g_s[r][c] = (uint8_t)gray_of(b[0], b[1], b[2]);
   }
 }
 
@@ -209,11 +252,14 @@ template <int RB, int TW>
 __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs a) {
   static_assert(RB * TW == kThreads * 16, "one 16-pixel segment per thread");
   constexpr int GR = RB + 6, GC = TW + 6, QR = RB + 2, QC = TW + 2, P = TW + 8;
+  constexpr int RAW = (3 * GC + 3 + 4 + 3) / 4;  // words of one staged RGB row run
   __shared__ __align__(16) uint8_t g_s[GR][P];
+  __shared__ __align__(16) uint32_t raw_s[GR][RAW];
   __shared__ __align__(16) uint16_t v_s[QR][P];
   __shared__ __align__(16) uint8_t q_s[QR][P];
   __shared__ uint32_t whist[kWarps][256];
   __shared__ uint32_t s_item, s_flag;
+  stamp_entry(a.stamp);
   for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&whist[0][0])[i] = 0u;
   for (;;) {
     __syncthreads();
@@ -222,6 +268,7 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
     const uint32_t item = s_item;
     if (item >= a.total_items) {
       if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;  // last CTA out
+      stamp_exit(a.stamp);
       return;
     }
     const ImgJobDev& j = find_job(a, item);
@@ -229,10 +276,13 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
     const uint32_t local = item - j.item0;
     const int band = (int)(local / j.chunks), chunk = (int)(local - (uint32_t)band * j.chunks);
     const int y0 = band * RB;
-    const int xa = chunk * kImgChunkCols, xb = min(W, xa + kImgChunkCols);
+    const int xa = chunk * (int)j.chunk_cols, xb = min(W, xa + (int)j.chunk_cols);
     const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
     for (int x0 = xa; x0 < xb; x0 += TW) {
-      stage_gray<GR, GC, P>(g_s, j.rgb, W, H, y0 - 3, x0 - 3);
+      if (x0 - 3 >= 0 && x0 - 3 + GC <= W && (reinterpret_cast<uintptr_t>(j.rgb) & 3) == 0)
+        stage_gray_rows<GR, GC, P, RAW>(g_s, raw_s, j.rgb, W, H, y0 - 3, x0 - 3);
+      else
+        stage_gray<GR, GC, P>(g_s, j.rgb, W, H, y0 - 3, x0 - 3);
       __syncthreads();
       gauss_tile<QR, QC, GC, P, P, P>(q_s, g_s, v_s, W, H, y0 - 1, x0 - 1, y0 - 3, x0 - 3);
       __syncthreads();
@@ -244,6 +294,7 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
 }
 
 __global__ void __launch_bounds__(kThreads) gray_kernel(const GrayArgs a) {
+  stamp_entry(a.stamp);
   const size_t groups = (a.px + 15) / 16;
   const bool vec = ((reinterpret_cast<uintptr_t>(a.rgb) | reinterpret_cast<uintptr_t>(a.gray)) & 15) == 0;
   for (size_t g = (size_t)blockIdx.x * kThreads + threadIdx.x; g < groups; g += (size_t)gridDim.x * kThreads) {
@@ -264,6 +315,7 @@ __global__ void __launch_bounds__(kThreads) gray_kernel(const GrayArgs a) {
         a.gray[p] = (uint8_t)gray_of(a.rgb[3 * p], a.rgb[3 * p + 1], a.rgb[3 * p + 2]);
     }
   }
+  stamp_exit(a.stamp);
 }
 
 // One CTA per 32 x 128 output tile of the Gaussian image.
@@ -274,6 +326,7 @@ __global__ void __launch_bounds__(kThreads) gauss_kernel(const GaussArgs a) {
   __shared__ __align__(16) uint8_t q_s[kRB][P];
   const int W = (int)a.W, H = (int)a.H;
   const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kRB;
+  stamp_entry(a.stamp);
   stage_u8<GR, GC, P>(g_s, a.g, W, H, y0 - 2, x0 - 2);
   __syncthreads();
   gauss_tile<kRB, kTW, GC, P, P, P>(q_s, g_s, v_s, W, H, y0, x0, y0 - 2, x0 - 2);
@@ -282,6 +335,7 @@ __global__ void __launch_bounds__(kThreads) gauss_kernel(const GaussArgs a) {
     const int r = i / kTW, c = i - r * kTW;
     if (y0 + r < H && x0 + c < W) a.q[(size_t)(y0 + r) * W + x0 + c] = q_s[r][c];
   }
+  stamp_exit(a.stamp);
 }
 
 // Sobel + histogram over the Gaussian image: same work items, tiles and histogram protocol as
@@ -289,6 +343,7 @@ __global__ void __launch_bounds__(kThreads) gauss_kernel(const GaussArgs a) {
 __global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArgs sa) {
   const ImgFusedArgs& a = sa.a;
   const uint8_t* __restrict__ q = sa.q;
+  stamp_entry(sa.stamp);
   constexpr int QR = kRB + 2, QC = kTW + 2, P = kTW + 8;
   __shared__ __align__(16) uint8_t q_s[QR][P];
   __shared__ uint32_t whist[kWarps][256];
@@ -304,11 +359,12 @@ __global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArg
     const uint32_t item = s_item;
     if (item >= a.total_items) {
       if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;
+      stamp_exit(sa.stamp);
       return;
     }
     const int band = (int)(item / j.chunks), chunk = (int)(item - (uint32_t)band * j.chunks);
     const int y0 = band * kRB;
-    const int xa = chunk * kImgChunkCols, xb = min(W, xa + kImgChunkCols);
+    const int xa = chunk * (int)j.chunk_cols, xb = min(W, xa + (int)j.chunk_cols);
     for (int x0 = xa; x0 < xb; x0 += kTW) {
       stage_u8<QR, QC, P>(q_s, q, W, H, y0 - 1, x0 - 1);
       __syncthreads();
@@ -321,8 +377,8 @@ __global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArg
 
 constexpr int kTileRows[3] = {32, 16, 64};  // tile variants: 32x128, 16x256, 64x64
 
-uint32_t items_of(uint32_t W, uint32_t H, uint32_t* chunks, int rows = kRB) {
-  *chunks = (W + kImgChunkCols - 1) / kImgChunkCols;
+uint32_t items_of(uint32_t W, uint32_t H, uint32_t* chunks, int rows = kRB, uint32_t cols = kImgChunkCols) {
+  *chunks = (W + cols - 1) / cols;
   return ((H + rows - 1) / rows) * *chunks;
 }
 
@@ -353,7 +409,8 @@ ImgJobDev job_dev(const JobPlanIn& in, const JobLayout& L) {
   j.W = W;
   j.H = H;
   j.item0 = 0;
-  j.nitems = items_of(W, H, &j.chunks);
+  j.chunk_cols = kTW;  // one launch per image: one tile per work item spreads the image over more SMs
+  j.nitems = items_of(W, H, &j.chunks, kRB, j.chunk_cols);
   j.slot_gen = in.slot_gen;
   return j;
 }
@@ -394,21 +451,21 @@ bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   const size_t px = (size_t)W * H;
   uint8_t* gray = static_cast<uint8_t*>(in.d_scratch);
   uint8_t* gauss = gray + align256(px);
-  GrayArgs ga{j.rgb, gray, px};
+  GrayArgs ga{Stamp{}, j.rgb, gray, px};
   KernelLaunch& k0 = kl[0];
   k0.func = reinterpret_cast<const void*>(&gray_kernel);
   k0.grid = dim3((unsigned)std::min<size_t>((px + 16 * kThreads - 1) / (16 * kThreads), (size_t)sm_count() * 8));
   k0.block = dim3(kThreads);
   k0.deps = 0;
   set_args(k0, ga);
-  GaussArgs qa{gray, gauss, W, H};
+  GaussArgs qa{Stamp{}, gray, gauss, W, H};
   KernelLaunch& k1 = kl[1];
   k1.func = reinterpret_cast<const void*>(&gauss_kernel);
   k1.grid = dim3((W + kTW - 1) / kTW, (H + kRB - 1) / kRB);
   k1.block = dim3(kThreads);
   k1.deps = 1u << 0;
   set_args(k1, qa);
-  SobelHistArgs sa{fa, gauss};
+  SobelHistArgs sa{Stamp{}, fa, gauss};
   KernelLaunch& k2 = kl[2];
   k2.func = reinterpret_cast<const void*>(&sobel_hist_kernel);
   k2.grid = dim3(grid);
@@ -444,7 +501,8 @@ bool plan_img_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
     jd.W = W;
     jd.H = H;
     jd.item0 = item;
-    jd.nitems = items_of(W, H, &jd.chunks, kTileRows[variant]);
+    jd.chunk_cols = kImgChunkCols;  // many jobs per launch: wider items, fewer histogram flushes
+    jd.nitems = items_of(W, H, &jd.chunks, kTileRows[variant], jd.chunk_cols);
     jd.slot_gen = slot_gen;
     item += jd.nitems;
     std::memcpy(h_table + desc_off + (size_t)j * sizeof(ImgJobDev), &jd, sizeof jd);

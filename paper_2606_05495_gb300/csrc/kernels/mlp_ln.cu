@@ -17,6 +17,7 @@
 // never issued), the producer waits for its own copies before the CTA leaves, and TMEM is always
 // freed.  The last GEMM2 CTA (done counter) writes the trailer with the error bits and resets the
 // control block.
+#include <cooperative_groups.h>
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -27,6 +28,8 @@
 #include "../runtime/thread_error.h"
 #include "stages.h"
 #include "tc.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace setk {
 namespace {
@@ -53,6 +56,7 @@ struct TrailerRec {  // batched form: one per job of the launch
 static_assert(sizeof(TrailerRec) == kMlpTrailerRecBytes, "trailer record size shared with the layout code");
 
 struct GemmArgs {
+  Stamp stamp;  // first member: filled by the planner
   CUtensorMap ta;  // A: rows x K, K-major, box {64, 128}
   CUtensorMap tb;  // B: N x K, K-major, box {64, BN}
   void* out;       // GELU: bf16 [M][N]; JOIN: f32 [M][N]
@@ -67,6 +71,7 @@ struct GemmArgs {
 };
 
 struct LnArgs {
+  Stamp stamp;  // first member: filled by the planner
   const uint16_t* x;  // bf16 [M][1024]
   float* y;           // f32 [M][1024]
   uint32_t M;
@@ -82,6 +87,33 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 __device__ __forceinline__ float gelu_erf(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 
+// Epilogue of NV consecutive outputs of one row: GELU -> BF16 (GEMM1) or + LayerNorm -> FP32 (join).
+template <int EPI, int NV>
+__device__ __forceinline__ void store_row(const GemmArgs& p, int row, int col, const float (&v)[NV]) {
+  static_assert(NV % 8 == 0, "whole 16-byte stores");
+  if constexpr (EPI == kEpiGelu) {
+    uint16_t* dst = static_cast<uint16_t*>(p.out) + (size_t)row * p.N + col;
+#pragma unroll
+    for (int q = 0; q < NV / 8; ++q) {
+      uint4 w;
+      w.x = pack_bf16x2(gelu_erf(v[8 * q + 0]), gelu_erf(v[8 * q + 1]));
+      w.y = pack_bf16x2(gelu_erf(v[8 * q + 2]), gelu_erf(v[8 * q + 3]));
+      w.z = pack_bf16x2(gelu_erf(v[8 * q + 4]), gelu_erf(v[8 * q + 5]));
+      w.w = pack_bf16x2(gelu_erf(v[8 * q + 6]), gelu_erf(v[8 * q + 7]));
+      reinterpret_cast<uint4*>(dst)[q] = w;
+    }
+  } else {
+    float* dst = static_cast<float*>(p.out) + (size_t)row * p.N + col;
+    const float* add = p.addend + (size_t)row * p.N + col;
+#pragma unroll
+    for (int q = 0; q < NV / 4; ++q) {
+      const float4 a = reinterpret_cast<const float4*>(add)[q];
+      reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q] + a.x, v[4 * q + 1] + a.y, v[4 * q + 2] + a.z,
+                                                      v[4 * q + 3] + a.w);
+    }
+  }
+}
+
 template <int BN, int STAGES>
 struct GemmSmem {
   static constexpr size_t kA = (size_t)kBM * kBK * 2;  // 16 KiB per stage
@@ -90,9 +122,14 @@ struct GemmSmem {
   static constexpr size_t kBytes = kTiles + 1024 /*alignment*/ + 256 /*barriers*/;
 };
 
-template <int BN, int STAGES, int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_constant__ GemmArgs p) {
+// SPLIT > 1: split-K over a cluster of SPLIT CTAs along z (each takes K / SPLIT); the FP32
+// partial tiles are parked in each CTA's shared memory and rank r reduces rows
+// [r * 128 / SPLIT, (r + 1) * 128 / SPLIT) over distributed shared memory before the epilogue.
+template <int BN, int STAGES, int EPI, int SPLIT>
+__global__ void __cluster_dims__(1, 1, SPLIT) __launch_bounds__(kGemmThreads, 2)
+    mlp_gemm_kernel(const __grid_constant__ GemmArgs p) {
   using SM = GemmSmem<BN, STAGES>;
+  static_assert(SPLIT == 1 || (size_t)kBM * BN * 4 <= SM::kTiles, "the partial tile fits the stage buffers");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -104,9 +141,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_
   uint32_t* s_err = s_tmem + 1;
   uint32_t* s_last = s_tmem + 2;
 
+  stamp_entry(p.stamp);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
-  const int nk = (int)(p.K / kBK);
+  const int nk = (int)(p.K / kBK) / SPLIT;
+  const int kb0 = (int)blockIdx.z * nk;  // this CTA's share of K (in 64-wide blocks)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -138,8 +177,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_
         break;
       }
       tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(SM::kA + SM::kB));
-      tc::tma_load_2d(sA + s * SM::kA, &p.ta, &full[s], kb * kBK, m0);
-      tc::tma_load_2d(sB + s * SM::kB, &p.tb, &full[s], kb * kBK, n0);
+      tc::tma_load_2d(sA + s * SM::kA, &p.ta, &full[s], (kb0 + kb) * kBK, m0);
+      tc::tma_load_2d(sB + s * SM::kB, &p.tb, &full[s], (kb0 + kb) * kBK, n0);
       issued = kb + 1;
     }
     // before the CTA can leave, every copy it started must have landed
@@ -169,40 +208,61 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_
   const bool acc_ok = tc::mbar_wait(accum, 0, kWaitLimit);
   tc::fence_after_sync();
   if (!acc_ok) atomicOr(s_err, 1u);
-  const int row = m0 + warp * 32 + lane;
-  const bool row_ok = row < (int)p.M;
+  if constexpr (SPLIT == 1) {
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < (int)p.M;
 #pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
-    uint32_t r[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-    tc::tmem_ld_wait();
-    if (!acc_ok || !row_ok) continue;
-    const int col = n0 + c * 32;
-    if constexpr (EPI == kEpiGelu) {
-      uint16_t* dst = static_cast<uint16_t*>(p.out) + (size_t)row * p.N + col;
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t r[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+      tc::tmem_ld_wait();
+      if (!acc_ok || !row_ok) continue;
+      float v[32];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint4 v;
-        v.x = pack_bf16x2(gelu_erf(__uint_as_float(r[8 * q + 0])), gelu_erf(__uint_as_float(r[8 * q + 1])));
-        v.y = pack_bf16x2(gelu_erf(__uint_as_float(r[8 * q + 2])), gelu_erf(__uint_as_float(r[8 * q + 3])));
-        v.z = pack_bf16x2(gelu_erf(__uint_as_float(r[8 * q + 4])), gelu_erf(__uint_as_float(r[8 * q + 5])));
-        v.w = pack_bf16x2(gelu_erf(__uint_as_float(r[8 * q + 6])), gelu_erf(__uint_as_float(r[8 * q + 7])));
-        reinterpret_cast<uint4*>(dst)[q] = v;
-      }
-    } else {
-      float* dst = static_cast<float*>(p.out) + (size_t)row * p.N + col;
-      const float* add = p.addend + (size_t)row * p.N + col;
+      for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+      store_row<EPI, 32>(p, row, n0 + c * 32, v);
+    }
+  } else {
+    // park the partial tile (row-major [128][BN] FP32) in this CTA's stage buffers: every MMA
+    // has completed (accum barrier) and every TMA copy has landed (the producer drained them)
+    __syncthreads();
+    float* part = reinterpret_cast<float*>(smem);
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t r[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+      tc::tmem_ld_wait();
+      float* dst = part + (size_t)(warp * 32 + lane) * BN + c * 32;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 a = reinterpret_cast<const float4*>(add)[q];
-        float4 v;
-        v.x = __uint_as_float(r[4 * q + 0]) + a.x;
-        v.y = __uint_as_float(r[4 * q + 1]) + a.y;
-        v.z = __uint_as_float(r[4 * q + 2]) + a.z;
-        v.w = __uint_as_float(r[4 * q + 3]) + a.w;
-        reinterpret_cast<float4*>(dst)[q] = v;
+      for (int q = 0; q < 32; q += 4)
+        *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
+                                                          __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+    }
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    // rank r sums rows [r * 128 / SPLIT, ...) over the SPLIT partials; 4 threads per row
+    constexpr int kRows = kBM / SPLIT, kTpr = kGemmThreads / kRows, kCols = BN / kTpr;
+    static_assert(kGemmThreads % kRows == 0 && BN % kTpr == 0 && kCols % 8 == 0, "reduction mapping");
+    const int rr = (int)cluster.block_rank() * kRows + threadIdx.x / kTpr;
+    const int c0 = (threadIdx.x % kTpr) * kCols;
+    const int row = m0 + rr;
+    float v[kCols];
+#pragma unroll
+    for (int q = 0; q < kCols; ++q) v[q] = 0.f;
+#pragma unroll 1
+    for (int src = 0; src < SPLIT; ++src) {  // fixed order: the sum is the same in every run
+      const float* rp = cluster.map_shared_rank(part, src) + (size_t)rr * BN + c0;
+#pragma unroll
+      for (int q = 0; q < kCols; q += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(rp + q);
+        v[q] += t.x;
+        v[q + 1] += t.y;
+        v[q + 2] += t.z;
+        v[q + 3] += t.w;
       }
     }
+    if (acc_ok && row < (int)p.M) store_row<EPI, kCols>(p, row, n0 + c0, v);
+    cluster.sync();  // keep every partial alive until all ranks have read it
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -211,7 +271,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_
   if constexpr (EPI == kEpiJoin) {
     if (threadIdx.x == 0) {
       __threadfence();
-      *s_last = atomicAdd(&p.ctl->done, 1u) == gridDim.x * gridDim.y - 1;
+      *s_last = atomicAdd(&p.ctl->done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
     }
     __syncthreads();
     if (*s_last) {
@@ -238,12 +298,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) mlp_gemm_kernel(const __grid_
       }
     }
   }
+  stamp_exit(p.stamp);
 }
 
 // One warp per row of 1024: two-pass mean / variance in registers.
 __global__ void __launch_bounds__(256) layernorm_kernel(const LnArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t row = blockIdx.x * 8 + warp;
+  stamp_entry(a.stamp);  // thread 0 is warp 0, whose row always exists
   if (row >= a.M) return;
   const uint4* src = reinterpret_cast<const uint4*>(a.x + (size_t)row * kMlpD);
   float v[32];
@@ -280,11 +342,14 @@ __global__ void __launch_bounds__(256) layernorm_kernel(const LnArgs a) {
     dst[2 * (lane + 32 * i) + 1] = make_float4((v[8 * i + 4] - mean) * inv, (v[8 * i + 5] - mean) * inv,
                                                (v[8 * i + 6] - mean) * inv, (v[8 * i + 7] - mean) * inv);
   }
+  stamp_exit(a.stamp);
 }
 
 // ---- host side ----
-constexpr int kBN1 = 128, kStages1 = 4;  // GEMM1: 1024 -> 4096
-constexpr int kBN2 = 64, kStages2 = 6;   // GEMM2: 4096 -> 1024 (narrower tiles: more CTAs)
+// Stage rings of 96 KiB let two CTAs share an SM (one's epilogue overlaps the other's main loop).
+constexpr int kBN1 = 128, kStages1 = 3;  // GEMM1: 1024 -> 4096
+constexpr int kBN2 = 64, kStages2 = 4;   // GEMM2: 4096 -> 1024 (narrower tiles: more CTAs)
+constexpr int kSplit2 = 4;               // GEMM2 split-K for one job (m <= 256: 16 N-tiles only)
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -343,10 +408,10 @@ bool weight_map(CUtensorMap* m, const void* w, uint64_t k, uint64_t rows, uint32
   return true;
 }
 
-template <int BN, int STAGES, int EPI>
+template <int BN, int STAGES, int EPI, int SPLIT = 1>
 void fill_gemm(KernelLaunch& k, const GemmArgs& a, uint32_t deps) {
-  k.func = reinterpret_cast<const void*>(&mlp_gemm_kernel<BN, STAGES, EPI>);
-  k.grid = dim3(a.N / BN, (a.M + kBM - 1) / kBM);
+  k.func = reinterpret_cast<const void*>(&mlp_gemm_kernel<BN, STAGES, EPI, SPLIT>);
+  k.grid = dim3(a.N / BN, (a.M + kBM - 1) / kBM, SPLIT);
   k.block = dim3(kGemmThreads);
   k.smem = (unsigned)GemmSmem<BN, STAGES>::kBytes;
   k.deps = deps;
@@ -365,7 +430,7 @@ bool plan_mlp_ln(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int*
   float* ln = reinterpret_cast<float*>(static_cast<uint8_t*>(in.d_scratch) + align256(mp * kMlpF * 2));
   MlpCtl* ctl = static_cast<MlpCtl*>(in.d_persist);
 
-  LnArgs la{x, ln, m};
+  LnArgs la{Stamp{}, x, ln, m};
   KernelLaunch& k0 = kl[0];
   k0.func = reinterpret_cast<const void*>(&layernorm_kernel);
   k0.grid = dim3((m + 7) / 8);
@@ -394,18 +459,26 @@ bool plan_mlp_ln(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int*
   g2.N = kMlpD;
   g2.K = kMlpF;
   fill_gemm<kBN1, kStages1, kEpiGelu>(kl[1], g1, 0);
-  fill_gemm<kBN2, kStages2, kEpiJoin>(kl[2], g2, (1u << 0) | (1u << 1));
+  fill_gemm<kBN2, kStages2, kEpiJoin, kSplit2>(kl[2], g2, (1u << 0) | (1u << 1));
   *nk = 3;
   return true;
 }
 
 cudaError_t mlp_init() {
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&mlp_gemm_kernel<kBN1, kStages1, kEpiGelu>),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)GemmSmem<kBN1, kStages1>::kBytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&mlp_gemm_kernel<kBN2, kStages2, kEpiJoin>),
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmSmem<kBN2, kStages2>::kBytes);
+  const struct {
+    const void* f;
+    size_t smem;
+  } fs[] = {
+      {reinterpret_cast<const void*>(&mlp_gemm_kernel<kBN1, kStages1, kEpiGelu, 1>), GemmSmem<kBN1, kStages1>::kBytes},
+      {reinterpret_cast<const void*>(&mlp_gemm_kernel<kBN2, kStages2, kEpiJoin, 1>), GemmSmem<kBN2, kStages2>::kBytes},
+      {reinterpret_cast<const void*>(&mlp_gemm_kernel<kBN2, kStages2, kEpiJoin, kSplit2>),
+       GemmSmem<kBN2, kStages2>::kBytes},
+  };
+  for (const auto& f : fs) {
+    const cudaError_t e = cudaFuncSetAttribute(f.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Batched form: the rows of nb jobs packed into one M = sum(m_j + 1); the same three kernels run
@@ -432,7 +505,7 @@ bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
   const uint16_t* x = reinterpret_cast<const uint16_t*>(d_block + x_off);
   uint16_t* h = reinterpret_cast<uint16_t*>(d_block + h_off);
   float* ln = reinterpret_cast<float*>(d_block + ln_off);
-  LnArgs la{x, ln, M};
+  LnArgs la{Stamp{}, x, ln, M};
   KernelLaunch& k0 = kl[0];
   k0.func = reinterpret_cast<const void*>(&layernorm_kernel);
   k0.grid = dim3((M + 7) / 8);

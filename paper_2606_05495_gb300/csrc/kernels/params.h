@@ -24,6 +24,7 @@ constexpr int kImgMaxBatch = 4096;           // jobs of one batched launch
 // Slot control block: [image state (fixed) | scan state (grows with the slot)].
 constexpr uint32_t kCtlImgOff = 0;
 constexpr uint32_t kCtlMlpOff = 1536;        // MLP job state {err, done} inside the fixed region
+constexpr uint32_t kCtlStampOff = 1664;      // stamps mode: {arrive, depart} per kernel of the job
 constexpr uint32_t kCtlImgBytes = 2048;
 constexpr uint32_t kCtlScanOff = kCtlImgBytes;
 

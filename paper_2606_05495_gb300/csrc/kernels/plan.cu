@@ -6,18 +6,26 @@ namespace setk {
 bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
   JobLayout L;
   if (!job_sizes(in.type, in.dims, &L)) return false;
+  bool ok = false;
   switch (in.type) {
     case SET_JOB_BLUR_HIST:
-      return plan_blur_hist(in, L, kl, nk);
+      ok = plan_blur_hist(in, L, kl, nk);
+      break;
     case SET_JOB_SAXPY_SCAN_MAX:
-      return plan_saxpy_scan_max(in, L, kl, nk);
+      ok = plan_saxpy_scan_max(in, L, kl, nk);
+      break;
     case SET_JOB_IMG_SOBEL_HIST:
-      return plan_img_sobel_hist(in, L, kl, nk);
+      ok = plan_img_sobel_hist(in, L, kl, nk);
+      break;
     case SET_JOB_MLP_LN:
-      return plan_mlp_ln(in, L, kl, nk);
+      ok = plan_mlp_ln(in, L, kl, nk);
+      break;
     default:
       return false;
   }
+  if (ok)
+    for (int k = 0; k < *nk; ++k) attach_stamp(kl[k], in.stamps, k);
+  return ok;
 }
 
 cudaError_t kernels_init() {

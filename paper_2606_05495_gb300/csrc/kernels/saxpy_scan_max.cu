@@ -45,6 +45,7 @@ static_assert(sizeof(ScanHdr) == kScanHdrBytes, "scan header size shared with th
 static_assert(kScanBytesPerTile == 16, "status word + max word per tile");
 
 struct ScanArgs {
+  Stamp stamp;  // first member: filled by the planner
   const float* x;
   const float* y;
   float* z;
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   // tile = blockIdx.x: blocks are dispatched in index order, so every tile a look-back waits for
   // has started.  The epoch load is issued first and only consumed by the look-back, so its
   // latency overlaps the data loads.
+  stamp_entry(p.stamp);
   const uint32_t tile = blockIdx.x;
   const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&hdr->epoch) & 0x3FFFFFFFu;
   const uint32_t n = p.n;
@@ -225,7 +227,10 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tm = fmaxf(tm, __shfl_xor_sync(0xFFFFFFFFu, tm, o));
   if (lane == 0) st_relaxed(&maxw[tile], max_word(epoch, tm));
-  if (tile != p.T - 1) return;
+  if (tile != p.T - 1) {
+    stamp_exit(p.stamp);
+    return;
+  }
 
   // last tile: gather every tile's max word (32 per round), write m and the trailer, then
   // recycle the scratch (new epoch, clear err): every tile has finished its look-back by now
@@ -262,6 +267,7 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
     p.trailer->word = trailer_word(err);
     hdr->epoch = (epoch + 1u) & 0x3FFFFFFFu;
   }
+  stamp_exit(p.stamp);
 }
 
 inline uint32_t num_tiles(uint32_t n) { return (n + kTile - 1) / kTile; }

@@ -17,6 +17,35 @@
 
 namespace setk {
 
+// Stage-order stamps (a test invariant, off unless the context enables it): the first CTA of a
+// kernel to arrive writes an entry ticket and the last CTA to leave writes an exit ticket, both
+// drawn from one device counter, into the slot's mapped host array.  Every kernel's argument
+// struct starts with a Stamp so that the planner can fill it generically.
+struct Stamp {
+  unsigned long long* clock = nullptr;  // device ticket counter (null: stamps off)
+  uint32_t* ctr = nullptr;              // device {arrive, depart} counters of this kernel
+  uint64_t* out = nullptr;              // mapped host {entry, exit} of this kernel
+  uint64_t pad = 0;
+};
+static_assert(sizeof(Stamp) == 32, "stamp header of every argument struct");
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void stamp_entry(const Stamp& s) {
+  if (s.clock && threadIdx.x == 0 && atomicAdd(&s.ctr[0], 1u) == 0u)
+    *reinterpret_cast<volatile uint64_t*>(&s.out[0]) = atomicAdd(s.clock, 1ull) + 1ull;  // tickets start at 1
+}
+__device__ __forceinline__ void stamp_exit(const Stamp& s) {
+  if (s.clock && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&s.ctr[1], 1u) == gridDim.x * gridDim.y * gridDim.z - 1u) {
+      *reinterpret_cast<volatile uint64_t*>(&s.out[1]) = atomicAdd(s.clock, 1ull) + 1ull;
+      s.ctr[0] = 0u;  // every CTA has arrived and left: ready for the next launch
+      s.ctr[1] = 0u;
+    }
+  }
+}
+#endif
+
 constexpr int kMaxKernels = 6;
 constexpr size_t kMaxArgBytes = 512;  // room for two 128-byte TMA descriptors
 
@@ -42,7 +71,18 @@ struct JobPlanIn {
   uint64_t job_id = 0;
   uint32_t slot_gen = 0;
   int img_fused = 1;
+  Stamp stamps;  // base of this slot's stamps (ctr / out point at kernel 0), clock null = off
 };
+
+// Fills the Stamp header of kernel k's arguments from a slot's stamp base.
+inline void attach_stamp(KernelLaunch& k, const Stamp& base, int idx) {
+  Stamp st = base;
+  if (st.clock) {
+    st.ctr = base.ctr + 2 * idx;
+    st.out = base.out + 2 * idx;
+  }
+  __builtin_memcpy(k.args, &st, sizeof st);
+}
 
 // Fills kl[0 .. *nk) with the job's kernel launches in dependency order.
 bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk);

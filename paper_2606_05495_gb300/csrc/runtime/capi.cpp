@@ -76,6 +76,7 @@ void set_config_default(set_config* c) {
   c->batch_max = 1;
   c->img_ctas_per_sm = 4;
   c->img_tile = 0;
+  c->stamps = 0;
   c->arena_bytes = 0;
 }
 

@@ -50,6 +50,8 @@ struct SlotState {
   GraphInst gi[SET_NUM_JOB_TYPES + 1];
   BatchGraph bg[SET_NUM_JOB_TYPES + 1];
   uint8_t* h_table = nullptr;  // pinned staging of the batch table (written at dispatch)
+  uint64_t* h_stamps = nullptr;  // stamps mode: mapped host {entry, exit} x kernels
+  uint64_t* d_stamps = nullptr;  // its device alias
   cudaEvent_t done = nullptr;
 };
 
@@ -119,6 +121,22 @@ class CudaDevice final : public Device {
   bool plan_batch(Slot& s, const setk::BatchItem* items, int nb, const setk::BatchLayout& L, uint8_t* d_block,
                   const void* const shared[2], setk::KernelLaunch* kl, int* nk);
   uint8_t* batch_block(Slot& s) { return s.job_mem ? s.job_mem : s.dev + ctl_; }
+  setk::Stamp stamp_base(const Slot& s) const {
+    setk::Stamp st;
+    if (clock_) {
+      st.clock = clock_;
+      st.ctr = reinterpret_cast<uint32_t*>(s.dev + setk::kCtlStampOff);
+      st.out = st_[s.index].d_stamps;
+    }
+    return st;
+  }
+  // Before a launch: clear the slot's stamp array and remember the kernels' dependencies.
+  void arm_stamps(Slot& s, const setk::KernelLaunch* kl, int nk) {
+    if (!clock_) return;
+    for (int k = 0; k < 2 * setk::kMaxKernels; ++k) st_[s.index].h_stamps[k] = 0;
+    s.stamp_nk = nk;
+    for (int k = 0; k < nk; ++k) s.stamp_deps[k] = kl[k].deps;
+  }
   bool plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::KernelLaunch* kl, int* nk) const;
   set_status update(const Slot& s, const JobRec& j, GraphInst& gi, LaunchCost* cost, std::string* err);
   void release();
@@ -134,6 +152,7 @@ class CudaDevice final : public Device {
   size_t ctl_ = 0;
   bool supported_[SET_NUM_JOB_TYPES + 1] = {};
   std::atomic<int> img_ctas_{4}, img_tile_{0};  // batched image kernel launch shape (autotuned)
+  unsigned long long* clock_ = nullptr;          // stamps mode: the ticket counter
   cudaMemcpyKind kind_in_ = cudaMemcpyHostToDevice, kind_out_ = cudaMemcpyDeviceToHost;
 };
 
@@ -145,6 +164,10 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
   SET_CK(cudaFree(nullptr));
   SET_CK(setk::kernels_init());
   ctl_ = setk::slot_control_bytes(cfg.slot_bytes);
+  if (cfg.stamps) {
+    SET_CK(cudaMalloc(&clock_, sizeof(unsigned long long)));
+    SET_CK(cudaMemset(clock_, 0, sizeof(unsigned long long)));
+  }
   // arena mode: slots keep only the kernels' control state; payloads live in the arena
   const size_t stride = cfg.arena_bytes ? setk::align256(ctl_) : setk::align256(cfg.slot_bytes);
   const size_t need = stride * slots.size();
@@ -190,6 +213,14 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
     s.bytes = cfg.arena_bytes ? stride : cfg.slot_bytes;
     s.dev_state = &st_[s.index];
     SET_CK(cudaEventCreateWithFlags(&st_[s.index].done, cudaEventDisableTiming));
+    if (cfg.stamps) {
+      SlotState& ss = st_[s.index];
+      SET_CK(cudaHostAlloc(reinterpret_cast<void**>(&ss.h_stamps), 2 * setk::kMaxKernels * sizeof(uint64_t),
+                           cudaHostAllocMapped));
+      SET_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ss.d_stamps), ss.h_stamps, 0));
+      std::memset(ss.h_stamps, 0, 2 * setk::kMaxKernels * sizeof(uint64_t));
+      s.stamps = ss.h_stamps;
+    }
     s.job_mem = static_cast<uint8_t*>(arena_);  // templates point into the arena (never launched as built)
     for (uint32_t t = 1; t <= SET_NUM_JOB_TYPES; ++t) {
       if (!(cfg.type_mask & (1u << t))) continue;
@@ -229,6 +260,7 @@ bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::
   in.job_id = j.id;
   in.slot_gen = s.gen;
   in.img_fused = cfg_.img_fused;
+  in.stamps = stamp_base(s);
   return setk::plan_job(in, kl, nk);
 }
 
@@ -298,6 +330,7 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
   }
   uint8_t* base = s.job_mem ? s.job_mem : s.dev;
   const uint64_t t0 = now_ns();
+  arm_stamps(const_cast<Slot&>(s), kl, nk);
   cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
   if (e == cudaSuccess)
     for (int k = 0; k < nk && e == cudaSuccess; ++k) {
@@ -360,8 +393,13 @@ bool CudaDevice::plan_batch(Slot& s, const setk::BatchItem* items, int nb, const
   if (L.table_bytes > kTableStaging) return false;
   if (items && nb > 0 && L.nb == nb) {
     // the type was fixed when the layout was made: image and MLP tables differ in shape
-    if (L.rows) return setk::plan_mlp_batch(items, nb, L, d_block, ss.h_table, s.gen, shared[0], shared[1], kl, nk);
-    return setk::plan_img_batch(items, nb, L, d_block, ss.h_table, s.gen, img_ctas_.load(), img_tile_.load(), kl, nk);
+    const bool ok =
+        L.rows ? setk::plan_mlp_batch(items, nb, L, d_block, ss.h_table, s.gen, shared[0], shared[1], kl, nk)
+               : setk::plan_img_batch(items, nb, L, d_block, ss.h_table, s.gen, img_ctas_.load(), img_tile_.load(), kl,
+                                      nk);
+    if (ok)
+      for (int k = 0; k < *nk; ++k) setk::attach_stamp(kl[k], stamp_base(s), k);
+    return ok;
   }
   return false;
 }
@@ -447,6 +485,7 @@ set_status CudaDevice::launch_batch(Slot& s, bool callback, LaunchCost* cost, st
     *err = std::string("batch does not match its graph template: ") + setrt::thread_error_text();
     return SET_EINVAL;
   }
+  arm_stamps(s, kl, nk);
   cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(bg.exec, bg.table, d_block, ss.h_table, L.table_bytes,
                                                      cudaMemcpyHostToDevice);
   for (int j = 0; j < (int)bg.h2d.size() && e == cudaSuccess; ++j) {
@@ -624,6 +663,7 @@ void CudaDevice::release() {
       if (bg.graph) cudaGraphDestroy(bg.graph);
     }
     if (ss.h_table) cudaFreeHost(ss.h_table);
+    if (ss.h_stamps) cudaFreeHost(ss.h_stamps);
     if (ss.done) cudaEventDestroy(ss.done);
   }
   st_.clear();
@@ -635,6 +675,8 @@ void CudaDevice::release() {
   pool_ = nullptr;
   if (arena_) cudaFree(arena_);
   arena_ = nullptr;
+  if (clock_) cudaFree(clock_);
+  clock_ = nullptr;
   if (ph_host_) cudaFreeHost(ph_host_);
   if (ph_dev_) cudaFree(ph_dev_);
   ph_host_ = ph_dev_ = nullptr;

@@ -427,6 +427,20 @@ void Executor::finish_job(Slot& s, const JobRec& j, int32_t dev_status, uint64_t
 // Algorithm 3: ++c_done (per job of the slot), return the slot to W_pool, wake one dispatcher.
 void Executor::on_complete(Slot& s, int32_t dev_status) {
   const uint64_t t = now_ns();
+  if (cfg_.stamps && s.stamps && dev_status == SET_OK && s.stamp_nk > 0) {
+    // per-job stage order: every kernel started after each kernel it depends on had finished
+    bool ok = true;
+    for (int k = 0; k < s.stamp_nk; ++k) {
+      const uint64_t entry = s.stamps[2 * k], exit = s.stamps[2 * k + 1];
+      if (entry == 0 || exit == 0 || entry > exit) ok = false;
+      for (int q = 0; q < k; ++q)
+        if ((s.stamp_deps[k] >> q) & 1u) ok = ok && s.stamps[2 * q + 1] < entry;
+    }
+    if (!ok) {
+      order_errors_.fetch_add(s.batch.empty() ? 1 : s.batch.size(), std::memory_order_relaxed);
+      dev_status = SET_EDEVICE;
+    }
+  }
   uint64_t n = 1;
   if (s.batch.empty()) {
     finish_job(s, s.job, dev_status, t);
@@ -486,6 +500,7 @@ void Executor::stats(set_stats_t* s) const {
   s->mean_update_us = nl ? (double)update_ns_.load() * 1e-3 / (double)nl : 0.0;
   s->mean_launch_us = nl ? (double)launch_ns_.load() * 1e-3 / (double)nl : 0.0;
   s->mem_waits = mem_waits_.load();
+  s->order_errors = order_errors_.load();
   s->arena_peak_bytes = use_arena_ ? const_cast<BuddyArena&>(arena_).peak() : 0;
 }
 
@@ -500,6 +515,7 @@ void Executor::reset_stats() {
   launch_ns_.store(0);
   launched_.store(0);
   mem_waits_.store(0);
+  order_errors_.store(0);
   t_first_ns_.store(0);
   t_last_ns_.store(0);
   lat_.reset();

@@ -39,6 +39,9 @@ struct Slot {
   size_t job_mem_bytes = 0;
   Slot* group_prev = nullptr;      // earlier slot of the same completion group (cb_every > 1)
   std::vector<JobRec> batch;       // batched form: the jobs of this launch (empty: the single `job`)
+  volatile uint64_t* stamps = nullptr;  // stamps mode: {entry, exit} per kernel (mapped host memory)
+  uint32_t stamp_deps[8] = {};          // dependency mask of each kernel of the launch
+  int stamp_nk = 0;
 };
 
 struct LaunchCost {
@@ -141,6 +144,7 @@ class Executor {
   std::atomic<uint64_t> t_first_ns_{0}, t_last_ns_{0};
   std::atomic<uint64_t> stat_base_submitted_{0}, stat_base_done_{0}, stat_base_failed_{0};
   std::atomic<uint64_t> mem_waits_{0};
+  std::atomic<uint64_t> order_errors_{0};
   LogHist lat_;
   BuddyArena arena_;
   bool use_arena_ = false;
