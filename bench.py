@@ -3,8 +3,8 @@
 
 Workload (the headline configuration): 4096 scan jobs, each saxpy -> exclusive prefix sum ->
 max|S| over n = 65536 fp32 elements (x, y uniform [-1, 1), per-job a uniform [-2, 2)), 512 KiB
-copied in and 512 KiB + 32 B copied out per job, 8 lane streams, 8 host dispatch workers, work
-stealing.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
+copied in and 512 KiB + 32 B copied out per job, 16 lane streams with rings of 4 slots, one host
+dispatch thread, work stealing, one completion callback per 8 launches of a lane.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
 launch, H2D copy, kernel, D2H copy, completion callback) until set_wait_all returns.
 
 Printed JSON line:
@@ -44,6 +44,10 @@ UNIT = "jobs/s"
 N_ELEM = 65536
 JOB_IN = 8 * N_ELEM
 JOB_OUT = 8 * N_ELEM + 32
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of saxpy_scan_max_kernel, mean of three
+# launches of one ncu capture (profiles/saxpy_scan_max_kernel__scan_n65536.md); reset to None
+# whenever the kernel changes until it is captured again
+SCAN_TRAFFIC_BYTES = 542976
 
 
 def parse():
@@ -118,14 +122,26 @@ def shard(njobs: int, rank: int):
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
-    """nvidia-smi samples every 200 ms during the timed region."""
+    """SM clock and clock-event reasons, sampled only while a timed region runs (`with
+    clocks.window():`).  NVML through ctypes, read-only queries every 10 ms from a thread; if NVML
+    cannot be opened, nvidia-smi every 200 ms over the whole span instead."""
 
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
+        import threading
+        self.index, self.rows, self.p = index, [], None
+        self._on, self._quit = threading.Event(), threading.Event()
+        self.nvml, self.h = self._open_nvml(index)
+        if self.nvml is not None:
+            self.th = threading.Thread(target=self._loop, daemon=True)
+            self.th.start()
+            return
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
@@ -134,7 +150,64 @@ class Clocks:
         except OSError:
             self.p = None
 
+    @staticmethod
+    def _open_nvml(index):
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None, None
+            h = ctypes.c_void_p()
+            t = _torch()
+            pr = t.cuda.get_device_properties(index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0 and \
+                    lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                return None, None
+            return lib, h
+        except (OSError, AttributeError, RuntimeError):
+            return None, None
+
+    def _sample(self):
+        cur, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib, h = self.nvml, self.h
+        if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(cur)) != 0:  # NVML_CLOCK_SM
+            return
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        f = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if f(h, ctypes.byref(rs)) != 0:
+            rs.value = 0
+        self.rows.append((cur.value, mx.value, rs.value))
+
+    def _loop(self):
+        while not self._quit.is_set():
+            if self._on.wait(0.05) and not self._quit.is_set():
+                self._sample()
+                time.sleep(0.01)
+
+    def window(self):
+        """Context manager: samples are taken only inside it."""
+        import contextlib
+
+        @contextlib.contextmanager
+        def cm():
+            self._on.set()
+            try:
+                yield
+            finally:
+                self._on.clear()
+        return cm()
+
     def stop(self):
+        if self.nvml is not None:
+            self._quit.set()
+            self._on.set()
+            self.th.join()
+            sm = [r[0] for r in self.rows]
+            reasons = sorted({n for r in self.rows for b, n in self.REASONS.items() if r[2] & b})
+            return {"sm_mhz": statistics.median(sm) if sm else None,
+                    "sm_max_mhz": max(r[1] for r in self.rows) if self.rows else None,
+                    "samples": len(self.rows), "source": "nvml, 10 ms, timed regions only", "reasons": reasons}
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -148,7 +221,7 @@ class Clocks:
         reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]
                           and "Not" not in r[5 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(rows), "reasons": reasons}
+                "samples": len(rows), "source": "nvidia-smi, 200 ms", "reasons": reasons}
 
 
 # ---------------------------------------------------------------- the oracle (CPU baseline / reference)
@@ -156,7 +229,7 @@ class Clocks:
 def oracle_rate(job_ids, cpu_seconds: float, threads: int, max_distinct: int = 512):
     """CPU oracle jobs/s over a bounded sample: inputs are generated before timing (up to
     max_distinct distinct jobs, cycled), then jobs run on `threads` host threads (ctypes drops the
-    GIL) until about cpu_seconds of CPU work or the whole workload is done."""
+    GIL), about cpu_seconds of CPU work in all, cycling over the workload's jobs."""
     from concurrent.futures import ThreadPoolExecutor
 
     import datagen
@@ -172,7 +245,7 @@ def oracle_rate(job_ids, cpu_seconds: float, threads: int, max_distinct: int = 5
     t0 = time.perf_counter()
     one(0)
     per_job = time.perf_counter() - t0
-    n = max(threads, min(len(job_ids), int(cpu_seconds / max(per_job, 1e-6))))
+    n = max(threads, int(cpu_seconds / max(per_job, 1e-6)))  # cycles over the workload's jobs
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(one, range(n)))
@@ -248,7 +321,8 @@ def run_step(S, ctx, descs, n):
     S.check(S.set_wait_all(ctx, 600_000_000), "set_wait_all", ctx)
 
 
-def timed(S, ctx, descs, n, args, d: Dist):
+def timed(S, ctx, descs, n, args, d: Dist, clocks: "Clocks | None" = None):
+    import contextlib
     t = _torch()
     for _ in range(args.warmup):
         run_step(S, ctx, descs, n)
@@ -256,11 +330,12 @@ def timed(S, ctx, descs, n, args, d: Dist):
     d.barrier()
     t.cuda.synchronize()
     e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        run_step(S, ctx, descs, n)
-    e1.record()
-    t.cuda.synchronize()
+    with clocks.window() if clocks is not None else contextlib.nullcontext():
+        e0.record()
+        for _ in range(args.steps):
+            run_step(S, ctx, descs, n)
+        e1.record()
+        t.cuda.synchronize()
     d.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     st = S.set_stats_t()
@@ -337,8 +412,7 @@ def run_set(args, d: Dist):
     # value: inputs and outputs resident in HBM
     ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
     clocks = Clocks(dev_index)
-    ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d)
-    clk = clocks.stop()
+    ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d, clocks)
     S.set_destroy(ctx_dev)
 
     # e2e with one completion callback per job (Algorithm 3 as written), for reference
@@ -349,7 +423,8 @@ def run_set(args, d: Dist):
 
     # e2e: pinned host buffers, H2D/D2H inside the timed region
     ctx = S.create(S.default_config(io_mode=S.SET_IO_HOST, **cfg))
-    ms_host, st_host = timed(S, ctx, w.descs_host, nj, args, d)
+    ms_host, st_host = timed(S, ctx, w.descs_host, nj, args, d, clocks)
+    clk = clocks.stop()
     baselines = {}
     if not args.no_baselines:
         for name, kind in (("single_stream_loop", S.SET_BASE_SYNC), ("batch_sync_graph", S.SET_BASE_BATCH_SYNC)):
@@ -416,7 +491,7 @@ def run_set(args, d: Dist):
                                       "note": "cb_every=1: one completion callback per job"}},
         "gpu_launches": args.steps * nj * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "saxpy_scan_max_kernel",
+                     "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
                      "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
                      "alg_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "pipeline": {"copy_rates_gbs": rates, "bound_jobs_per_s": nj / bound_s,
@@ -429,11 +504,21 @@ def run_set(args, d: Dist):
                   for k, v in traces.items()},
         "baselines": baselines, "clocks": clk,
     }
+    # Eq. 4: t_schedule / T_measured = 1 - T_ideal / T_measured, T_ideal = the gap-free pipeline time
+    t_ideal_ms = bound_s * 1e3
+    sched = {"set_e2e": 1 - t_ideal_ms / ms_host, "set_per_job_callbacks": 1 - t_ideal_ms / ms_host1}
+    for k, v in baselines.items():
+        sched[k] = 1 - (nj / bound_s) / v["jobs_per_s"] if v["jobs_per_s"] > 0 else None
+    line["eq4_schedule_frac"] = sched
     if not args.no_cpu:
         threads = os.cpu_count() or 1
-        r, n, dt = oracle_rate(list(shard(args.jobs, 0)), 10.0, threads)
+        ids = list(shard(args.jobs, 0))
+        r, n, dt = oracle_rate(ids, 20.0, threads)  # about 20 s of CPU work over all threads
+        r1, n1, dt1 = oracle_rate(ids, 3.0, 1)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{n} scan jobs of the workload ({dt:.1f} s wall on {threads} threads)"}
+                                "sample": f"{n} scan jobs cycling over the workload's {len(ids)} "
+                                          f"({dt:.1f} s wall on {threads} threads)",
+                                "single_thread": {"value": r1, "jobs": n1, "seconds": dt1}}
     print(json.dumps(line), flush=True)
 
 
@@ -497,11 +582,11 @@ class JobSet:
         return sum(d[0] for d in self.dims)
 
 
-def _rate(S, cfg, descs, n, args, d):
+def _rate(S, cfg, descs, n, args, d, clocks=None):
     """jobs/s of the SET executor over `steps` timed steps, with the stats of those steps."""
     ctx = S.create(S.default_config(**cfg))
     try:
-        ms, st = timed(S, ctx, descs, n, args, d)
+        ms, st = timed(S, ctx, descs, n, args, d, clocks)
         return {"jobs_per_s": n / (ms * 1e-3), "ms_per_step": ms, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                 "failed": st["failed"], "canary_errors": st["canary_errors"]}
     finally:
@@ -527,6 +612,7 @@ def run_workload(args, d: Dist):
     line = {"workload": args.workload, "unit": "jobs/s", "steps": args.steps, "warmup": args.warmup,
             "data": "synthetic (seeded SplitMix64 inputs)"}
     common = dict(num_workers=1, cb_mode=0, device=d.local)
+    clocks = Clocks(d.local)
     if args.workload == "blur":
         # 64 jobs of 64 KiB last tens of microseconds: a step runs the 64-job configuration 200 times
         # over (12,800 distinct jobs, each with its own input and output)
@@ -534,7 +620,7 @@ def run_workload(args, d: Dist):
         js = JobSet(S, 1, range(n), device_copy=True)
         cfg = dict(common, num_streams=2, ring_depth=4, slot_bytes=js.slot_bytes(S))
         line["config"] = {"jobs_per_step": n, "side": 256, "streams": 2, "note": "64-job configuration x 200"}
-        line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d)
+        line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
         line["set_per_job_callbacks"] = _rate(S, dict(cfg, cb_every=1), js.descs, n, args, d)
         line["set_device_resident"] = _rate(S, dict(cfg, cb_every=8, io_mode=S.SET_IO_DEVICE), js.descs_dev, n, args, d)
         line["set_16_streams"] = _rate(S, dict(cfg, cb_every=8, num_streams=16), js.descs, n, args, d)
@@ -548,7 +634,7 @@ def run_workload(args, d: Dist):
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=sb)
         line["config"] = {"jobs": n, "sample_of": 10000 if kind == 3 else 2000, "streams": 16,
                           "in_bytes": js.bytes_in, "out_bytes": js.bytes_out}
-        line["set_per_job"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d)
+        line["set_per_job"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
         if kind == 3:
             line["set_per_stage_graphs"] = _rate(S, dict(cfg, cb_every=8, img_fused=0), js.descs, n, args, d)
         # batched form: autotuned jobs per launch (and tile / CTAs per SM for images) in an 8 GiB arena
@@ -557,7 +643,7 @@ def run_workload(args, d: Dist):
         tune = S.set_tune_result()
         ns = min(n, 64)
         S.check(S.set_autotune(ctx, kind, js.descs, ns, ctypes.byref(tune)), "set_autotune", ctx)
-        ms, st = timed(S, ctx, js.descs, n, args, d)
+        ms, st = timed(S, ctx, js.descs, n, args, d, clocks)
         S.set_destroy(ctx)
         line["set_batched"] = {"jobs_per_s": n / (ms * 1e-3), "ms_per_step": ms, "p99_us": st["p99_us"],
                                "failed": st["failed"], "autotune": tune.as_dict()}
@@ -579,9 +665,9 @@ def run_workload(args, d: Dist):
         for k in (1, 3, 4):
             pools[k] = JobSet(S, k, range(50000 + 100000 * k, 50000 + 100000 * k + counts[k]))
         cfg = dict(common, num_streams=16, ring_depth=4, cb_every=1, slot_bytes=64 << 20, arena_bytes=8 << 30)
-        cfg["cb_mode"] = 1  # host function on the lane stream: one hop less on the completion path
         line["config"] = {"arrivals_per_rate": npool, "mix": "40% blur 256x256, 40% image (log-uniform sides), "
-                          "20% MLP (m 1..256)", "arena_bytes": 8 << 30, "streams": 16}
+                          "20% MLP (m 1..256)", "arena_bytes": 8 << 30, "streams": 16, "ring_depth": 4,
+                          "workers": 1}
         sweep = []
         for lam in rates:
             ts, kinds, _ = datagen.serve_trace(lam, npool)
@@ -592,16 +678,23 @@ def run_workload(args, d: Dist):
                 used[int(k)] += 1
             off = (ctypes.c_uint64 * npool)(*[int(x * 1e9) for x in ts])
             row = {"rate": lam}
-            for name, mode in (("set", S.SET_SERVE_SET), ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC)):
-                ctx = S.create(S.default_config(**cfg))
+            # set: completion by the polling thread (cb_mode 3); set_host_callbacks: Algorithm 3's
+            # host function on the lane stream (cb_mode 1)
+            for name, mode, cbm in (("set", S.SET_SERVE_SET, 3), ("set_host_callbacks", S.SET_SERVE_SET, 1),
+                                    ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1)):
+                ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm)))
                 st = S.set_stats_t()
-                S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)
+                with clocks.window():
+                    S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)
                 S.set_destroy(ctx)
                 row[name] = {"jobs_per_s": st.jobs_per_s, "p50_us": st.p50_us, "p99_us": st.p99_us,
                              "failed": st.failed, "mem_waits": st.mem_waits}
+                if mode == S.SET_SERVE_SET:
+                    row[name].update(queue_us=st.mean_queue_us, service_us=st.mean_service_us)
             sweep.append(row)
             print(json.dumps(row), flush=True)
         line["sweep"] = sweep
+    line["clocks"] = clocks.stop()
     if d.rank == 0:
         print(json.dumps(line), flush=True)
 

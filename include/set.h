@@ -133,10 +133,13 @@ typedef struct {
   int cb_mode;         /* 0 (default): completion callback on a per-lane callback stream that waits
                           on an event recorded behind the graph (the lane never waits on the host);
                           1: cudaLaunchHostFunc directly on the lane stream;
-                          2: a host node at the end of every slot's graph (no extra call per job) */
+                          2: a host node at the end of every slot's graph (no extra call per job);
+                          3: no host function: an event recorded behind the graph, polled by a
+                          completion thread of the context that runs the completion path (lower
+                          latency, one host core busy while jobs are in flight) */
   int spin_us;         /* dispatch workers spin this long on an empty pool / queue before they
                           sleep on a futex (default 50; 0 = sleep at once) */
-  int cb_every;        /* cb_mode 0/1: attach one completion callback per this many jobs of a lane
+  int cb_every;        /* cb_mode 0/1/3: attach one completion callback per this many jobs of a lane
                           (it completes the whole group in stream order; default 1 = one per job).
                           Groups are closed early whenever a dispatch worker would wait. */
   int batch_max;       /* batched form: up to this many queued jobs of one batchable type (image,
@@ -167,6 +170,11 @@ typedef struct {
   uint64_t mem_waits;       /* arena mode: dispatches that waited for free memory */
   uint64_t order_errors;    /* stamps mode: jobs whose stage order was violated (should be 0) */
   uint64_t arena_peak_bytes;/* arena mode: peak bytes allocated */
+  double mean_queue_us;     /* arrival (submit) -> a dispatcher holds the job, a slot and (arena
+                               mode) its device memory, and starts launching it */
+  double mean_service_us;   /* launching starts -> the job's completion is handled on the
+                               host: parameter updates and launch calls, device time, callback
+                               delivery */
 } set_stats_t;
 
 /* ---- sizes ---- */

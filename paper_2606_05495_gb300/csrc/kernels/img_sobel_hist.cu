@@ -64,6 +64,7 @@ struct ImgFusedArgs {
   const ImgJobDev* table;  // device table of njobs entries, or nullptr: use `one`
   ImgHdr* hdr;
   uint32_t njobs, total_items;
+  uint32_t direct;  // 1: CTA b runs work item b once (grid = total_items), no ticket
   ImgJobDev one;
 };
 
@@ -101,41 +102,54 @@ __device__ void stage_gray(uint8_t (*g_s)[P], const uint8_t* __restrict__ rgb, i
   }
 }
 
-// stage_gray for a tile whose staged columns [x0, x0 + GC) lie inside the image: every staged row
-// is one contiguous run of 3 * GC bytes, fetched with aligned 4-byte loads into raw_s (the run
-// starts `lead` bytes into its first word), then converted from shared memory.  Rows are
-// clamped as before.  A run is only read up to its own last word, which never passes the end of
-// the image except on the image's last row; that row is fetched bytewise.
-template <int GR, int GC, int P, int RAW>
-__device__ void stage_gray_rows(uint8_t (*g_s)[P], uint32_t (*raw_s)[RAW], const uint8_t* __restrict__ rgb, int W,
-                                int H, int y0, int x0) {
-  constexpr int kBytes = 3 * GC;
-  static_assert(RAW * 4 >= kBytes + 3 + 4, "raw row holds the run and its alignment slack");
-  for (int i = threadIdx.x; i < GR * RAW; i += kThreads) {
-    const int r = i / RAW, w = i - r * RAW;
-    const int Y = clampi(y0 + r, H);
-    const uint8_t* run = rgb + 3 * ((size_t)Y * W + x0);
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(run) & ~uintptr_t(3);
-    const int lead = (int)(reinterpret_cast<uintptr_t>(run) - a0);
-    const int nwords = (lead + kBytes + 3) >> 2;
-    if (w >= nwords) continue;
-    if (Y == H - 1) {  // last image row: never read past the image's last byte
-      uint32_t v = 0;
-      for (int b = 0; b < 4; ++b) {
-        const intptr_t off = (intptr_t)(4 * w + b) - lead;
-        if (off >= 0 && off < kBytes) v |= (uint32_t)__ldg(run + off) << (8 * b);
-      }
-      raw_s[r][w] = v;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Words of 16 bytes that one staged RGB row run occupies in shared memory: up to 15 bytes of lead
+// (the run starts anywhere inside its first 16-byte word) plus 3 * GC bytes, rounded up.
+template <int GC>
+__host__ __device__ constexpr int raw_words() { return (15 + 3 * GC + 15) / 16; }
+
+// stage_gray for an RGB buffer that starts on a 16-byte boundary.  Staged row r holds the image
+// row cl(y0 + r) over the columns [xs, xe) = [x0, x0 + GC) clipped to the image; its bytes are
+// copied with 16-byte cp.async (all of a thread's copies in flight at once, one memory latency per
+// tile) from the 16-byte word that contains the run's first byte.  A copy whose word would pass
+// the end of the image is done bytewise, keeping only the run's own bytes.  The conversion then
+// reads the clamped column cl(x0 + c), which always lies in [xs, xe).
+template <int GR, int GC, int P, int RW>
+__device__ void stage_gray_async(uint8_t (*g_s)[P], uint4 (*raw_s)[RW], const uint8_t* __restrict__ rgb, int W,
+                                 int H, int y0, int x0) {
+  static_assert(RW >= raw_words<GC>(), "raw row holds the run and its lead");
+  const int xs = max(x0, 0), xe = min(x0 + GC, W);
+  const int nbytes = 3 * (xe - xs);
+  const uint8_t* end = rgb + 3 * (size_t)W * H;
+  for (int i = threadIdx.x; i < GR * RW; i += kThreads) {
+    const int r = i / RW, w = i - r * RW;
+    const uint8_t* run = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + xs);
+    const uint8_t* a0 = run - (reinterpret_cast<uintptr_t>(run) & 15);
+    const int lead = (int)(run - a0);
+    if (16 * w >= lead + nbytes) continue;
+    const uint8_t* src = a0 + 16 * w;
+    if (src + 16 <= end) {
+      cp_async16(&raw_s[r][w], src);
     } else {
-      raw_s[r][w] = __ldg(reinterpret_cast<const uint32_t*>(a0) + w);
+      uint8_t* dst = reinterpret_cast<uint8_t*>(&raw_s[r][w]);
+      for (int b = 0; b < 16; ++b) {
+        const int off = 16 * w + b - lead;
+        if (off >= 0 && off < nbytes) dst[b] = __ldg(src + b);
+      }
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   for (int i = threadIdx.x; i < GR * GC; i += kThreads) {
     const int r = i / GC, c = i - r * GC;
-    const uint8_t* run = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + x0);
-    const int lead = (int)(reinterpret_cast<uintptr_t>(run) & 3);
-    const uint8_t* b = reinterpret_cast<const uint8_t*>(raw_s[r]) + lead + 3 * c;
+    const uint8_t* run = rgb + 3 * ((size_t)clampi(y0 + r, H) * W + xs);
+    const int lead = (int)(reinterpret_cast<uintptr_t>(run) & 15);
+    const uint8_t* b = reinterpret_cast<const uint8_t*>(raw_s[r]) + lead + 3 * (clampi(x0 + c, W) - xs);
     g_s[r][c] = (uint8_t)gray_of(b[0], b[1], b[2]);
   }
 }
@@ -204,6 +218,22 @@ __device__ void sobel_tile(const uint8_t (*q_s)[QP], uint8_t* __restrict__ out, 
   for (int k = 0; k < nvalid; ++k) atomicAdd(&h[w][(o[k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
 }
 
+// Next work item of this CTA.  Direct launches: CTA b takes item b on its first pass.  Otherwise
+// items come from the atomic ticket; the last CTA to leave resets it.  False: the CTA is done.
+__device__ __forceinline__ bool next_item(const ImgFusedArgs& a, uint32_t pass, uint32_t* s_item, uint32_t* item) {
+  if (a.direct) {
+    *item = blockIdx.x;
+    return pass == 0 && blockIdx.x < a.total_items;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s_item = atomicAdd(&a.hdr->ticket, 1u);
+  __syncthreads();
+  *item = *s_item;
+  if (*item < a.total_items) return true;
+  if (threadIdx.x == 0 && *item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;
+  return false;
+}
+
 __device__ __forceinline__ const ImgJobDev& find_job(const ImgFusedArgs& a, uint32_t item) {
   if (!a.table) return a.one;
   uint32_t lo = 0, hi = a.njobs - 1;  // last job with item0 <= item
@@ -252,22 +282,19 @@ template <int RB, int TW>
 __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs a) {
   static_assert(RB * TW == kThreads * 16, "one 16-pixel segment per thread");
   constexpr int GR = RB + 6, GC = TW + 6, QR = RB + 2, QC = TW + 2, P = TW + 8;
-  constexpr int RAW = (3 * GC + 3 + 4 + 3) / 4;  // words of one staged RGB row run
+  constexpr int RW = raw_words<GC>();
   __shared__ __align__(16) uint8_t g_s[GR][P];
-  __shared__ __align__(16) uint32_t raw_s[GR][RAW];
+  __shared__ __align__(16) uint4 raw_s[GR][RW];
   __shared__ __align__(16) uint16_t v_s[QR][P];
   __shared__ __align__(16) uint8_t q_s[QR][P];
   __shared__ uint32_t whist[kWarps][256];
   __shared__ uint32_t s_item, s_flag;
   stamp_entry(a.stamp);
   for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&whist[0][0])[i] = 0u;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= a.total_items) {
-      if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;  // last CTA out
+  __syncthreads();
+  for (uint32_t pass = 0;; ++pass) {
+    uint32_t item;
+    if (!next_item(a, pass, &s_item, &item)) {
       stamp_exit(a.stamp);
       return;
     }
@@ -279,8 +306,8 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
     const int xa = chunk * (int)j.chunk_cols, xb = min(W, xa + (int)j.chunk_cols);
     const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
     for (int x0 = xa; x0 < xb; x0 += TW) {
-      if (x0 - 3 >= 0 && x0 - 3 + GC <= W && (reinterpret_cast<uintptr_t>(j.rgb) & 3) == 0)
-        stage_gray_rows<GR, GC, P, RAW>(g_s, raw_s, j.rgb, W, H, y0 - 3, x0 - 3);
+      if ((reinterpret_cast<uintptr_t>(j.rgb) & 15) == 0)
+        stage_gray_async<GR, GC, P, RW>(g_s, raw_s, j.rgb, W, H, y0 - 3, x0 - 3);
       else
         stage_gray<GR, GC, P>(g_s, j.rgb, W, H, y0 - 3, x0 - 3);
       __syncthreads();
@@ -352,13 +379,10 @@ __global__ void __launch_bounds__(kThreads) sobel_hist_kernel(const SobelHistArg
   const ImgJobDev& j = a.one;
   const int W = (int)j.W, H = (int)j.H;
   const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(j.out) & 15) == 0;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->ticket, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= a.total_items) {
-      if (threadIdx.x == 0 && item == a.total_items + gridDim.x - 1) a.hdr->ticket = 0u;
+  __syncthreads();
+  for (uint32_t pass = 0;; ++pass) {
+    uint32_t item;
+    if (!next_item(a, pass, &s_item, &item)) {
       stamp_exit(sa.stamp);
       return;
     }
@@ -435,8 +459,9 @@ bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   fa.hdr = static_cast<ImgHdr*>(in.d_persist);
   fa.njobs = 1;
   fa.total_items = j.nitems;
+  fa.direct = 1;  // one CTA per tile: the hardware schedules the waves, no ticket round trips
   fa.one = j;
-  const uint32_t grid = std::min<uint32_t>(j.nitems, (uint32_t)sm_count() * 4);
+  const uint32_t grid = j.nitems;
   if (in.img_fused) {
     KernelLaunch& k = kl[0];
     k.func = fused_func(0);

@@ -1,14 +1,20 @@
 // cuda_device.cpp -- the executor's CUDA side: slot pool, lane streams, one graph exec per
 // (slot, job type), per-job parameter updates, event-chained completion callbacks, direct
-// launches and the two baseline programming models (Sec. 4.1-4.2, Sec. 5.1.3).
+// launches and the two baseline programming models (Sec. 4.1-4.2, Sec. 5.1.3).  cb_mode 3 replaces
+// the host-function callback by a completion thread that queries each lane's oldest event.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../kernels/stages.h"
 #include "executor.h"
+#include "sync.h"
 #include "thread_error.h"
 
 namespace setrt {
@@ -154,7 +160,68 @@ class CudaDevice final : public Device {
   std::atomic<int> img_ctas_{4}, img_tile_{0};  // batched image kernel launch shape (autotuned)
   unsigned long long* clock_ = nullptr;          // stamps mode: the ticket counter
   cudaMemcpyKind kind_in_ = cudaMemcpyHostToDevice, kind_out_ = cudaMemcpyDeviceToHost;
+
+  // cb_mode 3: completion thread.  Dispatchers hand it (slot, event recorded behind the graph);
+  // it polls the oldest event of every lane (a lane's events complete in stream order) and runs
+  // the completion path itself, sleeping on a futex while nothing is in flight.
+  void poll_main();
+  void poll_push(Slot* s);
+  std::thread poller_;
+  std::atomic<bool> poll_stop_{false};
+  std::atomic<int64_t> poll_pending_{0};
+  Signal poll_sig_;
+  std::mutex poll_mu_;
+  std::vector<Slot*> poll_in_;
 };
+
+void CudaDevice::poll_push(Slot* s) {
+  poll_pending_.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> g(poll_mu_);
+    poll_in_.push_back(s);
+  }
+  poll_sig_.notify(1);
+}
+
+void CudaDevice::poll_main() {
+  thread_init();
+  std::vector<std::deque<Slot*>> fifo(lanes_.size());
+  std::vector<Slot*> got;
+  int idle_rounds = 0;
+  for (;;) {
+    const uint32_t seen = poll_sig_.load();
+    {
+      std::lock_guard<std::mutex> g(poll_mu_);
+      got.swap(poll_in_);
+    }
+    for (Slot* s : got) fifo[s->lane].push_back(s);
+    got.clear();
+    bool waiting = false, progressed = false;
+    for (auto& q : fifo) {
+      while (!q.empty()) {
+        Slot* s = q.front();
+        const cudaError_t e = cudaEventQuery(st_[s->index].done);
+        if (e == cudaErrorNotReady) {
+          waiting = true;
+          break;
+        }
+        if (e != cudaSuccess) cudaGetLastError();  // the job's trailer check reports the failure
+        q.pop_front();
+        progressed = true;
+        host_complete(s);
+        poll_pending_.fetch_sub(1);
+      }
+    }
+    if (waiting) {
+      // jobs in flight: poll again at once, yielding the core after a run of empty rounds
+      idle_rounds = progressed ? 0 : idle_rounds + 1;
+      if (idle_rounds > 64) std::this_thread::yield();
+      continue;
+    }
+    if (poll_stop_.load()) return;
+    poll_sig_.wait(seen, 100 * 1000000ll);
+  }
+}
 
 set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) {
   cfg_ = cfg;
@@ -240,6 +307,7 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
   }
   for (uint32_t t = 1; t <= SET_NUM_JOB_TYPES; ++t) supported_[t] = st_.empty() ? false : st_[0].gi[t].exec != nullptr;
   SET_CK(cudaDeviceSynchronize());
+  if (cfg.cb_mode == 3) poller_ = std::thread([this] { poll_main(); });
   return SET_OK;
 }
 
@@ -358,6 +426,9 @@ set_status CudaDevice::attach_callback(Slot& s, std::string* err) {
   cudaStream_t lane = lanes_[s.lane], cb = cbs_[s.lane];
   if (cfg_.cb_mode == 1) {
     SET_CK(cudaLaunchHostFunc(lane, host_complete, &s));
+  } else if (cfg_.cb_mode == 3) {
+    SET_CK(cudaEventRecord(ss.done, lane));
+    poll_push(&s);
   } else {
     SET_CK(cudaEventRecord(ss.done, lane));
     SET_CK(cudaStreamWaitEvent(cb, ss.done, 0));
@@ -649,10 +720,17 @@ set_status CudaDevice::autotune(uint32_t type, const JobRec* sample, size_t n, i
 void CudaDevice::drain() {
   for (auto s : lanes_) cudaStreamSynchronize(s);
   for (auto s : cbs_) cudaStreamSynchronize(s);
+  // cb_mode 3: every recorded event has completed; let the completion thread hand them back
+  for (int i = 0; i < 100000 && poll_pending_.load() > 0; ++i) std::this_thread::sleep_for(std::chrono::microseconds(100));
 }
 
 void CudaDevice::release() {
   drain();
+  if (poller_.joinable()) {
+    poll_stop_.store(true);
+    poll_sig_.notify_all();
+    poller_.join();
+  }
   for (auto& ss : st_) {
     for (auto& gi : ss.gi) {
       if (gi.exec) cudaGraphExecDestroy(gi.exec);

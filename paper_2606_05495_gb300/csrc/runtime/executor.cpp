@@ -44,8 +44,9 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   normalize(cfg);
   if (!out || cfg.num_streams < 1 || cfg.num_streams > 1024 || cfg.num_workers < 1 || cfg.num_workers > 256 ||
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
-      (cfg.io_mode != SET_IO_HOST && cfg.io_mode != SET_IO_DEVICE)) {
-    *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096)";
+      (cfg.io_mode != SET_IO_HOST && cfg.io_mode != SET_IO_DEVICE) || cfg.cb_mode < 0 || cfg.cb_mode > 3) {
+    *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
+           "cb_mode 0..3)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -302,6 +303,7 @@ void Executor::worker_main(int) {
     }
     space_sig_.notify(1);
     if (stolen) steals_.fetch_add(1, std::memory_order_relaxed);
+    s.t_dispatch_ns = 0;
     s.job = j;
     s.batch.clear();
     const int blim = batch_limit_.load(std::memory_order_relaxed);
@@ -344,6 +346,7 @@ void Executor::worker_main(int) {
       on_complete(s, sticky_.load());
       continue;
     }
+    s.t_dispatch_ns = now_ns();  // admitted: from here on the job is being launched
     LaunchCost cost;
     std::string e;
     s.group_prev = pending[s.lane];
@@ -420,6 +423,12 @@ void Executor::finish_job(Slot& s, const JobRec& j, int32_t dev_status, uint64_t
     }
   }
   lat_.record(t > j.t_submit_ns ? t - j.t_submit_ns : 0);
+  if (s.t_dispatch_ns) {
+    queue_ns_.fetch_add(s.t_dispatch_ns > j.t_submit_ns ? s.t_dispatch_ns - j.t_submit_ns : 0,
+                        std::memory_order_relaxed);
+    service_ns_.fetch_add(t > s.t_dispatch_ns ? t - s.t_dispatch_ns : 0, std::memory_order_relaxed);
+    timed_jobs_.fetch_add(1, std::memory_order_relaxed);
+  }
   if (st != SET_OK) c_failed_.fetch_add(1, std::memory_order_relaxed);
   if (j.d.status) *j.d.status = st;
 }
@@ -502,6 +511,9 @@ void Executor::stats(set_stats_t* s) const {
   s->mem_waits = mem_waits_.load();
   s->order_errors = order_errors_.load();
   s->arena_peak_bytes = use_arena_ ? const_cast<BuddyArena&>(arena_).peak() : 0;
+  const uint64_t nt = timed_jobs_.load();
+  s->mean_queue_us = nt ? (double)queue_ns_.load() * 1e-3 / (double)nt : 0.0;
+  s->mean_service_us = nt ? (double)service_ns_.load() * 1e-3 / (double)nt : 0.0;
 }
 
 void Executor::reset_stats() {
@@ -515,6 +527,9 @@ void Executor::reset_stats() {
   launch_ns_.store(0);
   launched_.store(0);
   mem_waits_.store(0);
+  queue_ns_.store(0);
+  service_ns_.store(0);
+  timed_jobs_.store(0);
   order_errors_.store(0);
   t_first_ns_.store(0);
   t_last_ns_.store(0);

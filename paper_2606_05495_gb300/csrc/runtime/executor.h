@@ -32,6 +32,7 @@ struct Slot {
   size_t bytes = 0;
   uint32_t gen = 0;       // bumped by every completion of this slot
   JobRec job{};           // job in flight
+  uint64_t t_dispatch_ns = 0;  // the dispatcher took the job (written before its launch)
   Executor* ex = nullptr;
   void* dev_state = nullptr;  // owned by the Device
   std::atomic<bool> quiet{false};  // set while a baseline reuses the slot's graphs: no completion path
@@ -141,6 +142,7 @@ class Executor {
   std::atomic<uint64_t> done_target_{~0ull};
   std::atomic<uint64_t> steals_{0}, updates_{0}, canary_errors_{0};
   std::atomic<uint64_t> update_ns_{0}, launch_ns_{0}, launched_{0};
+  std::atomic<uint64_t> queue_ns_{0}, service_ns_{0}, timed_jobs_{0};  // latency breakdown
   std::atomic<uint64_t> t_first_ns_{0}, t_last_ns_{0};
   std::atomic<uint64_t> stat_base_submitted_{0}, stat_base_done_{0}, stat_base_failed_{0};
   std::atomic<uint64_t> mem_waits_{0};

@@ -100,7 +100,7 @@ def test_baselines_compute_the_same_results(kind):
         (check_blur if j.type == s.SET_JOB_BLUR_HIST else check_scan)(j)
 
 
-@pytest.mark.parametrize("cb_mode", [0, 1, 2])
+@pytest.mark.parametrize("cb_mode", [0, 1, 2, 3])
 def test_callback_modes_and_baseline_reuse(cb_mode):
     s = S()
     jobs = [scan_job(k, n=20000 + k) for k in range(120)]
@@ -121,5 +121,26 @@ def test_callback_modes_and_baseline_reuse(cb_mode):
     finally:
         s.set_destroy(ctx)
     for j in jobs:
+        check_scan(j)
+    check_trailers(jobs)
+
+
+@pytest.mark.parametrize("cb_every", [1, 3])
+def test_polled_completion_destroy_with_jobs_in_flight(cb_every):
+    # cb_mode 3: the completion thread must hand back every job, also when the context is
+    # destroyed right after the last submit
+    s = S()
+    jobs = [scan_job(500 + k, n=30000 + 7 * k) for k in range(96)]
+    ctx = s.create(s.default_config(num_streams=3, num_workers=1, ring_depth=2, slot_bytes=1 << 20, cb_mode=3,
+                                    cb_every=cb_every))
+    arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+    first = ctypes.c_uint64()
+    try:
+        s.check(s.set_submit_many(ctx, arr, len(jobs), ctypes.byref(first), None), "submit", ctx)
+    finally:
+        s.set_destroy(ctx)
+    for k, j in enumerate(jobs):
+        j.id = first.value + k
+        assert j.status.value == 0, (k, j.status.value)
         check_scan(j)
     check_trailers(jobs)

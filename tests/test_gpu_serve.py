@@ -54,6 +54,15 @@ def test_serving_mix_equals_alone_and_oracle():
         s.set_destroy(ctx)
 
 
+def test_serving_polled_completion():
+    jobs, arrivals = serve_jobs(8000.0, 120, img_cap=1024)
+    st = _serve(jobs, arrivals, S().SET_SERVE_SET, cb_mode=3, **ARENA_CFG)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    assert 0 < st["mean_queue_us"] and st["mean_queue_us"] + st["mean_service_us"] >= 0.5 * st["p50_us"]
+    for j in jobs:
+        check_any(j)
+
+
 def test_serving_batch_sync_baseline_same_arrivals():
     jobs, arrivals = serve_jobs(4000.0, 80, img_cap=1024)
     st = _serve(jobs, arrivals, S().SET_SERVE_BATCH_SYNC, **ARENA_CFG)
