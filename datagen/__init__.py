@@ -15,6 +15,9 @@ Workloads (job payload layouts are the executor's input layouts):
   shared weights W1 [4096, 1024] ~ N(0, 1/1024), W2 [1024, 4096] ~ N(0, 1/4096),
   both stored out_features x in_features (h = x W1^T).
 * serve  (tag 5): Poisson arrivals (exponential gaps) and a 40/40/20 type mix.
+* hot    (tag 6): hotspot grid, T0 || P, two float32 R x C maps: T0 uniform [80, 90)
+  degrees, P uniform [0, 1e-3) watts per cell (512 x 512 cells, 64 steps in the
+  workload).
 """
 from __future__ import annotations
 
@@ -26,13 +29,16 @@ import threading
 import numpy as np
 
 MASTER_SEED = 2606055495
-TAG_BLUR, TAG_SCAN, TAG_IMG, TAG_MLP, TAG_SERVE = 1, 2, 3, 4, 5
+TAG_BLUR, TAG_SCAN, TAG_IMG, TAG_MLP, TAG_SERVE, TAG_HOT = 1, 2, 3, 4, 5, 6
 TAG_W1, TAG_W2 = 0x41, 0x42
 
 BLUR_SIDE = 256
 SCAN_N = 65536
 IMG_SIDE_MIN, IMG_SIDE_MAX = 128, 2048
 MLP_D, MLP_F, MLP_M_MAX = 1024, 4096, 256
+HOT_SIDE, HOT_STEPS = 512, 64
+HOT_T0 = (80.0, 90.0)
+HOT_P = (0.0, 1e-3)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libdatagen.so")
@@ -68,6 +74,8 @@ def lib() -> ctypes.CDLL:
             L.dg_fill_normal_bf16.argtypes, L.dg_fill_normal_bf16.restype = [u64, u64, dbl, vp, sz], None
             L.dg_logunif_side.argtypes, L.dg_logunif_side.restype = [u64, u64, i32, i32], i32
             L.dg_exp_gap.argtypes, L.dg_exp_gap.restype = [u64, u64, dbl], dbl
+            L.dg_fill_unif_range_f32.argtypes = [u64, u64, dbl, dbl, vp, sz]
+            L.dg_fill_unif_range_f32.restype = None
             _lib = L
     return _lib
 
@@ -148,6 +156,16 @@ def mlp_weights(master: int = MASTER_SEED, d: int = MLP_D, f: int = MLP_F):
 def bf16_to_f32(b: np.ndarray) -> np.ndarray:
     """Widen bf16 bit patterns to float32 (exact)."""
     return (b.astype(np.uint32) << 16).view(np.float32)
+
+
+def hot_job(j: int, R: int = HOT_SIDE, C: int = HOT_SIDE, out=None, master: int = MASTER_SEED) -> np.ndarray:
+    """T0 (R x C) followed by P (R x C), float32, of hotspot job j."""
+    o = _out(out, (2 * R * C,), np.float32)
+    s = job_seed(TAG_HOT, j, master)
+    L = lib()
+    L.dg_fill_unif_range_f32(s, 0, HOT_T0[0], HOT_T0[1], o.ctypes.data, R * C)
+    L.dg_fill_unif_range_f32(s, R * C, HOT_P[0], HOT_P[1], o[R * C:].ctypes.data, R * C)
+    return o
 
 
 SERVE_MIX = ((1, 0.4), (3, 0.4), (4, 0.2))  # (workload tag, share)

@@ -92,3 +92,11 @@ int dg_logunif_side(uint64_t seed, uint64_t idx, int lo, int hi) {
 double dg_exp_gap(uint64_t seed, uint64_t idx, double lambda) {
   return -log1p(-dg_unif01(seed, idx)) / lambda;
 }
+
+/* Uniform float in [lo, hi): lo + (hi - lo) * k * 2^-24 with k the top 24 bits,
+ * evaluated in double and rounded once to fp32. */
+void dg_fill_unif_range_f32(uint64_t seed, uint64_t off, double lo, double hi, float* out, size_t n) {
+#pragma omp parallel for schedule(static) if (n > (1u << 20))
+  for (size_t i = 0; i < n; ++i)
+    out[i] = (float)(lo + (hi - lo) * ((double)(uint32_t)(dg_rand(seed, off + i) >> 40) * 0x1.0p-24));
+}

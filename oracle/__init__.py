@@ -54,6 +54,8 @@ def lib() -> ctypes.CDLL:
                 "oracle_job_blur_hist": ([vp, i32, i32, vp, vp], None),
                 "oracle_job_saxpy_scan_max": ([f32, vp, vp, sz, vp, vp, vp], f64),
                 "oracle_job_img_sobel_hist": ([vp, i32, i32, vp, vp, vp, vp], None),
+                "oracle_hotspot_params": ([i32, i32, vp], None),
+                "oracle_hotspot": ([vp, vp, i32, i32, i32, vp], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -167,3 +169,20 @@ def job_mlp_ln(x_bf16: np.ndarray, w1_bf16: np.ndarray, w2_bf16: np.ndarray) -> 
     from datagen import bf16_to_f32
     return mlp.mlp_ln(bf16_to_f32(x_bf16).astype(np.float64), bf16_to_f32(w1_bf16).astype(np.float64),
                       bf16_to_f32(w2_bf16).astype(np.float64))
+
+
+def hotspot_params(R: int, C: int) -> dict:
+    """Model parameters of an R x C hotspot grid: conductances, capacity, time step, ambient."""
+    c = np.empty(6, np.float64)
+    lib().oracle_hotspot_params(R, C, c.ctypes.data)
+    return dict(zip(("gx", "gy", "gz", "cap", "dt", "t_amb"), (float(v) for v in c)))
+
+
+def hotspot(T0: np.ndarray, P: np.ndarray, K: int) -> np.ndarray:
+    """fp64 grid after K explicit steps of the hotspot model from T0 (R x C fp32) under P."""
+    T0, P = _c(T0, np.float32), _c(P, np.float32)
+    R, C = T0.shape
+    assert P.shape == (R, C)
+    T = np.empty((R, C), np.float64)
+    lib().oracle_hotspot(T0.ctypes.data, P.ctypes.data, R, C, K, T.ctypes.data)
+    return T

@@ -18,6 +18,7 @@
  *   scan job : z = fmaf(a, x, y) -> exclusive prefix sum S -> m = max |S_i|
  *   img job  : gray = (77R + 150G + 29B) >> 8 -> 5x5 Gaussian [1,4,6,4,1] (x) [1,4,6,4,1] >> 8
  *              -> Sobel min(|gx| + |gy|, 255) -> 256-bin histogram
+ *   hotspot  : K explicit Euler steps of a compact thermal RC grid (fp64 here)
  * (The MLP job's oracle is oracle/mlp.py, fp64 numpy.)
  * Every stencil clamps its own input image at the border (replicate edge).
  *
@@ -139,4 +140,71 @@ void oracle_job_img_sobel_hist(const uint8_t* rgb, int W, int H, uint8_t* gray, 
   oracle_gauss5(gray, W, H, gauss);
   oracle_sobel(gauss, W, H, sobel);
   oracle_hist256(sobel, (size_t)W * H, hist);
+}
+
+/* ---- hotspot job ----
+ *
+ * Sec. 5.1.2 names Hotspot (the HotSpot compact thermal model of Huang et al.,
+ * 2006): iterative thermal simulation.  The paper gives no parameters; the job
+ * is the model's R x C grid of cells over a silicon die, advanced K explicit
+ * Euler steps.  With dx = die width / C and dy = die height / R:
+ *   Gx  = k t dy / dx   conductance to each left / right neighbour
+ *   Gy  = k t dx / dy   conductance to each upper / lower neighbour
+ *   Gz  = k dx dy / t   conductance to the ambient through the die's thickness
+ *   Cap = c_v t dx dy   heat capacity of a cell
+ *   dt  = 0.2 Cap / (2 Gx + 2 Gy + Gz)   (a fifth of the scheme's positivity limit)
+ *   T'  = T + dt / Cap * (P + Gy (T_N + T_S - 2 T) + Gx (T_W + T_E - 2 T) + Gz (T_amb - T))
+ * A neighbour outside the die is the cell itself (adiabatic edges: no flux).
+ * Die 16 mm x 16 mm x 0.5 mm, k = 100 W/(m K), c_v = 1.75e6 J/(m^3 K),
+ * T_amb = 80.  T in degrees, P in watts per cell.  Evaluated in fp64 from the
+ * fp32 inputs, in the order written above. */
+#define ORACLE_HOT_DIE_W 0.016
+#define ORACLE_HOT_DIE_H 0.016
+#define ORACLE_HOT_THICK 0.0005
+#define ORACLE_HOT_K_SI 100.0
+#define ORACLE_HOT_CV_SI 1.75e6
+#define ORACLE_HOT_T_AMB 80.0
+#define ORACLE_HOT_DT_FRAC 0.2
+
+/* c = {Gx, Gy, Gz, Cap, dt, T_amb} of an R x C grid. */
+void oracle_hotspot_params(int R, int C, double* c) {
+  const double dx = ORACLE_HOT_DIE_W / C, dy = ORACLE_HOT_DIE_H / R;
+  const double gx = ORACLE_HOT_K_SI * ORACLE_HOT_THICK * dy / dx;
+  const double gy = ORACLE_HOT_K_SI * ORACLE_HOT_THICK * dx / dy;
+  const double gz = ORACLE_HOT_K_SI * dx * dy / ORACLE_HOT_THICK;
+  const double cap = ORACLE_HOT_CV_SI * ORACLE_HOT_THICK * dx * dy;
+  c[0] = gx;
+  c[1] = gy;
+  c[2] = gz;
+  c[3] = cap;
+  c[4] = ORACLE_HOT_DT_FRAC * cap / (2.0 * gx + 2.0 * gy + gz);
+  c[5] = ORACLE_HOT_T_AMB;
+}
+
+/* T (R*C doubles, row-major) = the grid after K steps from T0 under power P. */
+void oracle_hotspot(const float* T0, const float* P, int R, int C, int K, double* T) {
+  double c[6];
+  oracle_hotspot_params(R, C, c);
+  const double gx = c[0], gy = c[1], gz = c[2], cap = c[3], dt = c[4], tamb = c[5];
+  const size_t n = (size_t)R * C;
+  double* cur = (double*)malloc(n * sizeof(double));
+  double* nxt = (double*)malloc(n * sizeof(double));
+  for (size_t i = 0; i < n; ++i) cur[i] = (double)T0[i];
+  for (int step = 0; step < K; ++step) {
+    for (int i = 0; i < R; ++i)
+      for (int j = 0; j < C; ++j) {
+        const double t = cur[(size_t)i * C + j];
+        const double tn = cur[(size_t)clampi(i - 1, R) * C + j], ts = cur[(size_t)clampi(i + 1, R) * C + j];
+        const double tw = cur[(size_t)i * C + clampi(j - 1, C)], te = cur[(size_t)i * C + clampi(j + 1, C)];
+        const double p = (double)P[(size_t)i * C + j];
+        nxt[(size_t)i * C + j] =
+            t + dt / cap * (p + gy * (tn + ts - 2.0 * t) + gx * (tw + te - 2.0 * t) + gz * (tamb - t));
+      }
+    double* sw = cur;
+    cur = nxt;
+    nxt = sw;
+  }
+  memcpy(T, cur, n * sizeof(double));
+  free(cur);
+  free(nxt);
 }

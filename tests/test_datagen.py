@@ -39,3 +39,14 @@ def test_determinism_and_independence():
     t2, k2, _ = datagen.serve_trace(1000.0, 500)
     assert np.array_equal(t1, t2) and np.array_equal(k1, k2)
     assert set(np.unique(k1)) <= {1, 3, 4}
+
+
+def test_hotspot_inputs_ranges_and_determinism():
+    a = datagen.hot_job(11, 40, 70)
+    b = datagen.hot_job(11, 40, 70)
+    c = datagen.hot_job(12, 40, 70)
+    assert a.dtype == np.float32 and a.size == 2 * 40 * 70
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    T0, P = a[:2800], a[2800:]
+    assert T0.min() >= 80.0 and T0.max() < 90.0 and abs(float(T0.mean()) - 85.0) < 0.3
+    assert P.min() >= 0.0 and P.max() < 1e-3 and abs(float(P.mean()) - 5e-4) < 3e-5

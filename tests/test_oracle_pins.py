@@ -259,3 +259,88 @@ def test_mlp_job_bf16_widening_is_exact():
     x = datagen.bf16_to_f32(x_b[:, :8]).astype(np.float64)
     assert out.shape == (3, 8) and np.isfinite(out).all()
     assert np.allclose(out, mlp.mlp_ln(x, datagen.bf16_to_f32(w1), datagen.bf16_to_f32(w2)), rtol=1e-15)
+
+
+# ---- hotspot job: compact thermal RC grid, K explicit Euler steps ----
+
+def _hot_physics(R, C):
+    # die 16 mm x 16 mm x 0.5 mm, k = 100 W/(m K), c_v = 1.75e6 J/(m^3 K): slab conductances
+    dx, dy, t, k = 0.016 / C, 0.016 / R, 0.0005, 100.0
+    return dict(gx=k * t * dy / dx, gy=k * t * dx / dy, gz=k * dx * dy / t, cap=1.75e6 * t * dx * dy)
+
+
+@pytest.mark.parametrize("R,C", [(5, 7), (512, 512), (64, 300)])
+def test_hotspot_params_are_the_slab_conductances(R, C):
+    p, ph = oracle.hotspot_params(R, C), _hot_physics(R, C)
+    for key in ("gx", "gy", "gz", "cap"):
+        assert p[key] == pytest.approx(ph[key], rel=1e-14), key
+    # the step is a fifth of the positivity limit of the explicit scheme
+    assert p["dt"] * (2 * p["gx"] + 2 * p["gy"] + p["gz"]) / p["cap"] == pytest.approx(0.2, rel=1e-14)
+    assert p["t_amb"] == 80.0
+
+
+def test_hotspot_equilibrium_is_fixed():
+    T0 = np.full((6, 9), 80.0, np.float32)
+    T = oracle.hotspot(T0, np.zeros_like(T0), 7)
+    assert np.array_equal(T, np.full((6, 9), 80.0))
+
+
+@pytest.mark.parametrize("R,C,K", [(6, 9, 5), (3, 1, 11), (1, 1, 4)])
+def test_hotspot_uniform_fields_closed_form(R, C, K):
+    # a uniform field never has lateral flux (adiabatic edges), so each cell follows the scalar
+    # recurrence x' = x + dt/Cap (p - Gz x) with x = T - T_amb:
+    #   x_K = (1 - a)^K x_0 + (p / Gz) (1 - (1 - a)^K),  a = dt Gz / Cap
+    ph = _hot_physics(R, C)
+    p = oracle.hotspot_params(R, C)
+    a = p["dt"] * ph["gz"] / ph["cap"]
+    for T0v, Pv in ((90.0, 0.0), (80.0, 1e-3), (84.5, 3e-4)):
+        T0 = np.full((R, C), T0v, np.float32)
+        P = np.full((R, C), Pv, np.float32)
+        x0, pw = float(np.float32(T0v)) - 80.0, float(np.float32(Pv))
+        xK = (1 - a) ** K * x0 + pw / ph["gz"] * (1 - (1 - a) ** K)
+        assert np.allclose(oracle.hotspot(T0, P, K), 80.0 + xK, rtol=0, atol=1e-12)
+
+
+def _path_laplacian(n):
+    A = np.eye(n, k=1) + np.eye(n, k=-1)
+    return np.diag(A.sum(axis=1)) - A
+
+
+@pytest.mark.parametrize("R,C,K", [(5, 7, 4), (1, 6, 3), (8, 1, 2), (4, 4, 6)])
+def test_hotspot_matches_graph_laplacian_iteration(R, C, K):
+    # the same model as a linear map on the flattened grid: lateral coupling through the
+    # Laplacians of the row and column path graphs (no edges leave the die = adiabatic edges),
+    # T' = T + dt/Cap (P - (Gx Lx + Gy Ly) T - Gz (T - T_amb)).  Non-square cells make Gx != Gy,
+    # so a transposed neighbour or a swapped conductance fails.
+    rng = np.random.default_rng(R * 100 + C)
+    T0 = rng.uniform(80, 90, (R, C)).astype(np.float32)
+    P = rng.uniform(0, 1e-3, (R, C)).astype(np.float32)
+    ph = _hot_physics(R, C)
+    dt = oracle.hotspot_params(R, C)["dt"]
+    Lx = np.kron(np.eye(R), _path_laplacian(C))
+    Ly = np.kron(_path_laplacian(R), np.eye(C))
+    M = ph["gx"] * Lx + ph["gy"] * Ly
+    T = T0.astype(np.float64).ravel()
+    for _ in range(K):
+        T = T + dt / ph["cap"] * (P.astype(np.float64).ravel() - M @ T - ph["gz"] * (T - 80.0))
+    assert np.allclose(oracle.hotspot(T0, P, K).ravel(), T, rtol=0, atol=1e-10)
+
+
+def test_hotspot_heat_balance_and_max_principle():
+    # lateral flux only moves heat between cells: sum(T - T_amb) follows the scalar recurrence of
+    # a single cell driven by the total power; and with P = 0 the scheme (coefficients positive,
+    # summing to at most one) keeps every value inside the range of T0 and T_amb
+    R, C, K = 37, 53, 9
+    rng = np.random.default_rng(7)
+    T0 = rng.uniform(80, 90, (R, C)).astype(np.float32)
+    P = rng.uniform(0, 1e-3, (R, C)).astype(np.float32)
+    ph = _hot_physics(R, C)
+    a = oracle.hotspot_params(R, C)["dt"] * ph["gz"] / ph["cap"]
+    b = oracle.hotspot_params(R, C)["dt"] / ph["cap"]
+    s = float((T0.astype(np.float64) - 80.0).sum())
+    for _ in range(K):
+        s = (1 - a) * s + b * float(P.astype(np.float64).sum())
+    T = oracle.hotspot(T0, P, K)
+    assert (T - 80.0).sum() == pytest.approx(s, rel=1e-11)
+    T = oracle.hotspot(T0, np.zeros_like(P), K)
+    assert T.min() >= 80.0 and T.max() <= float(T0.max())
