@@ -3,8 +3,8 @@
 
 Workload (the headline configuration): 4096 scan jobs, each saxpy -> exclusive prefix sum ->
 max|S| over n = 65536 fp32 elements (x, y uniform [-1, 1), per-job a uniform [-2, 2)), 512 KiB
-copied in and 512 KiB + 32 B copied out per job, 16 lane streams with rings of 4 slots, one host
-dispatch thread, work stealing, one completion callback per 8 launches of a lane.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
+copied in and 512 KiB + 32 B copied out per job, 16 lane streams with rings of 4 slots, four host
+dispatch threads, work stealing, completion detected by a thread polling each lane's oldest event.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
 launch, H2D copy, kernel, D2H copy, completion callback) until set_wait_all returns.
 
 Printed JSON line:
@@ -58,16 +58,17 @@ def parse():
     p.add_argument("--impl", choices=["set", "reference"], default="set")
     p.add_argument("--jobs", type=int, default=4096)
     p.add_argument("--streams", type=int, default=16)
-    p.add_argument("--workers", type=int, default=1, help="host dispatch threads (1 is fastest on Grace)")
+    p.add_argument("--workers", type=int, default=4, help="host dispatch threads")
     p.add_argument("--ring", type=int, default=4)
-    p.add_argument("--cb-mode", type=int, default=0)
-    p.add_argument("--cb-every", type=int, default=8, help="jobs per completion callback and lane")
+    p.add_argument("--cb-mode", type=int, default=3, help="completion path (set_config.cb_mode); 3 = polled events")
+    p.add_argument("--cb-every", type=int, default=1, help="jobs per completion callback and lane")
     p.add_argument("--no-baselines", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve"], default="scan",
+    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot"], default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
+    p.add_argument("--clock-ms", type=float, default=25.0, help="clock sampling period in timed regions")
     p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
     return p.parse_args()
 
@@ -123,8 +124,8 @@ def shard(njobs: int, rank: int):
 
 class Clocks:
     """SM clock and clock-event reasons, sampled only while a timed region runs (`with
-    clocks.window():`).  NVML through ctypes, read-only queries every 10 ms from a thread; if NVML
-    cannot be opened, nvidia-smi every 200 ms over the whole span instead."""
+    clocks.window():`).  NVML through ctypes, read-only queries every period_ms from a thread; if
+    NVML cannot be opened, nvidia-smi every 200 ms over the whole span instead."""
 
     # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
@@ -133,9 +134,9 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: float = 25.0):
         import threading
-        self.index, self.rows, self.p = index, [], None
+        self.index, self.rows, self.p, self.period = index, [], None, period_ms * 1e-3
         self._on, self._quit = threading.Event(), threading.Event()
         self.nvml, self.h = self._open_nvml(index)
         if self.nvml is not None:
@@ -183,7 +184,7 @@ class Clocks:
         while not self._quit.is_set():
             if self._on.wait(0.05) and not self._quit.is_set():
                 self._sample()
-                time.sleep(0.01)
+                time.sleep(self.period)
 
     def window(self):
         """Context manager: samples are taken only inside it."""
@@ -207,7 +208,7 @@ class Clocks:
             reasons = sorted({n for r in self.rows for b, n in self.REASONS.items() if r[2] & b})
             return {"sm_mhz": statistics.median(sm) if sm else None,
                     "sm_max_mhz": max(r[1] for r in self.rows) if self.rows else None,
-                    "samples": len(self.rows), "source": "nvml, 10 ms, timed regions only", "reasons": reasons}
+                    "samples": len(self.rows), "source": f"nvml, {self.period * 1e3:g} ms, timed regions only", "reasons": reasons}
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -411,15 +412,18 @@ def run_set(args, d: Dist):
 
     # value: inputs and outputs resident in HBM
     ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
-    clocks = Clocks(dev_index)
+    clocks = Clocks(dev_index, args.clock_ms)
     ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d, clocks)
     S.set_destroy(ctx_dev)
 
-    # e2e with one completion callback per job (Algorithm 3 as written), for reference
-    c1 = dict(cfg, cb_every=1)
-    ctx1 = S.create(S.default_config(io_mode=S.SET_IO_HOST, **c1))
-    ms_host1, st_host1 = timed(S, ctx1, w.descs_host, nj, argparse.Namespace(warmup=2, steps=min(3, args.steps)), d)
-    S.set_destroy(ctx1)
+    # e2e with Algorithm 3's host-function callbacks (cb_mode 0, one dispatch thread): one per job
+    # as written, and one per group of 8 launches of a lane
+    host_cb = {}
+    for name, every in (("per_job", 1), ("groups_of_8", 8)):
+        c1 = dict(cfg, cb_mode=0, cb_every=every, num_workers=1)
+        ctx1 = S.create(S.default_config(io_mode=S.SET_IO_HOST, **c1))
+        host_cb[name] = timed(S, ctx1, w.descs_host, nj, argparse.Namespace(warmup=2, steps=min(3, args.steps)), d)
+        S.set_destroy(ctx1)
 
     # e2e: pinned host buffers, H2D/D2H inside the timed region
     ctx = S.create(S.default_config(io_mode=S.SET_IO_HOST, **cfg))
@@ -487,8 +491,10 @@ def run_set(args, d: Dist):
                 "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
                 "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
                 "steals": st_host["steals"],
-                "per_job_callbacks": {"value": world * nj / (ms_host1 * 1e-3), "p99_us": st_host1["p99_us"],
-                                      "note": "cb_every=1: one completion callback per job"}},
+                "host_callbacks": {k: {"value": world * nj / (v[0] * 1e-3), "p99_us": v[1]["p99_us"],
+                                       "mean_launch_us": v[1]["mean_launch_us"]} for k, v in host_cb.items()},
+                "note": "completion by polled events (cb_mode 3); host_callbacks: cudaLaunchHostFunc on a "
+                        "callback stream (cb_mode 0), one dispatch thread"},
         "gpu_launches": args.steps * nj * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
@@ -506,9 +512,10 @@ def run_set(args, d: Dist):
     }
     # Eq. 4: t_schedule / T_measured = 1 - T_ideal / T_measured, T_ideal = the gap-free pipeline time
     t_ideal_ms = bound_s * 1e3
-    sched = {"set_e2e": 1 - t_ideal_ms / ms_host, "set_per_job_callbacks": 1 - t_ideal_ms / ms_host1}
+    sched = {"set_e2e": 1 - t_ideal_ms / ms_host}
+    sched.update({f"set_host_callbacks_{k}": 1 - t_ideal_ms / v[0] for k, v in host_cb.items()})
     for k, v in baselines.items():
-        sched[k] = 1 - (nj / bound_s) / v["jobs_per_s"] if v["jobs_per_s"] > 0 else None
+        sched[k] = 1 - v["jobs_per_s"] / (nj / bound_s)
     line["eq4_schedule_frac"] = sched
     if not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -539,6 +546,8 @@ class JobSet:
                 self.dims.append((256, 256))
             elif kind == 3:
                 self.dims.append(dims[k] if dims else datagen.img_dims(j))
+            elif kind == 5:
+                self.dims.append(dims[k] if dims else (datagen.HOT_SIDE, datagen.HOT_SIDE, datagen.HOT_STEPS))
             else:
                 self.dims.append((dims[k] if dims else datagen.mlp_rows(j),))
         ib = [S.set_job_in_bytes(kind, S.dims4(*d)) for d in self.dims]
@@ -554,6 +563,9 @@ class JobSet:
                 datagen.blur_job(j, out=seg)
             elif kind == 3:
                 datagen.img_job(j, out=seg, dims=self.dims[k])
+            elif kind == 5:
+                C, R, _ = self.dims[k]
+                datagen.hot_job(j, R, C, out=seg.view(np.float32))
             else:
                 datagen.mlp_job(j, out=seg.view(np.uint16), m=self.dims[k][0])
         self.shared = (None, None)
@@ -612,7 +624,7 @@ def run_workload(args, d: Dist):
     line = {"workload": args.workload, "unit": "jobs/s", "steps": args.steps, "warmup": args.warmup,
             "data": "synthetic (seeded SplitMix64 inputs)"}
     common = dict(num_workers=1, cb_mode=0, device=d.local)
-    clocks = Clocks(d.local)
+    clocks = Clocks(d.local, args.clock_ms)
     if args.workload == "blur":
         # 64 jobs of 64 KiB last tens of microseconds: a step runs the 64-job configuration 200 times
         # over (12,800 distinct jobs, each with its own input and output)
@@ -652,6 +664,51 @@ def run_workload(args, d: Dist):
             flop = 2.0 * js.rows() * 1024 * 4096 * 2
             line["gemm_tflops_e2e"] = {k: flop / (line[k]["ms_per_step"] * 1e-3) / 1e12
                                        for k in ("set_per_job", "set_batched")}
+    elif args.workload == "hot":
+        # hotspot: 512 x 512 cells, 64 steps per job (8 temporally blocked launches of 8 steps)
+        n = min(args.jobs, 1000)
+        js = JobSet(S, 5, range(n), device_copy=True)
+        C, R, K = js.dims[0]
+        cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=js.slot_bytes(S))
+        line["config"] = {"jobs": n, "grid": [R, C], "steps": K, "streams": 16, "in_bytes": js.bytes_in,
+                          "out_bytes": js.bytes_out, "l2": "inputs > L2 (no flush needed)"}
+        line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
+        line["set_polled_2_workers"] = _rate(S, dict(cfg, cb_mode=3, num_workers=2), js.descs, n, args, d, clocks)
+        line["set_device_resident"] = _rate(S, dict(cfg, cb_mode=3, num_workers=2, io_mode=S.SET_IO_DEVICE),
+                                            js.descs_dev, n, args, d, clocks)
+        line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
+        line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
+        # the kernel chain alone: CUDA events around each job's 8 launches on one stream
+        st = t.cuda.Stream()
+        scratch = t.zeros(S.set_job_scratch_bytes(5, S.dims4(C, R, K)), dtype=t.uint8, device="cuda")
+        m = min(n, 256)
+        evs = [(t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)) for _ in range(m)]
+        with t.cuda.stream(st):
+            for k in range(8):
+                dd = js.descs_dev[k]
+                S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st.cuda_stream),
+                        "launch")
+            st.synchronize()
+            t.cuda._sleep(int(2e9 * 60e-6 * m))  # hold the stream while the launches are enqueued
+            for k in range(m):
+                dd = js.descs_dev[k]
+                evs[k][0].record(st)
+                S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st.cuda_stream)
+                evs[k][1].record(st)
+        st.synchronize()
+        job_us = statistics.mean(a.elapsed_time(b) * 1e3 for a, b in evs)
+        launch_us = job_us / 8
+        alg = 12 * R * C  # per launch: read T and P, write T
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        peak = peaks.get("hbm_gbs", 6800.0)
+        line["roofline"] = {"bound": "hbm", "kernel": "hotspot_kernel", "achieved": alg / (launch_us * 1e-6) / 1e9,
+                            "peak": peak, "unit": "GB/s", "frac": alg / (launch_us * 1e-6) / 1e9 / peak,
+                            "alg_bytes_per_launch": alg, "launch_us": launch_us, "job_us": job_us,
+                            "cell_steps_per_s": R * C * K / (job_us * 1e-6)}
     elif args.workload == "serve":
         import numpy as np
 

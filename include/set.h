@@ -74,15 +74,22 @@ typedef enum {
  *   out: float out[m][1024] = GELU(x W1^T) W2^T + LayerNorm(x), then the trailer.
  *        W1 is bf16 [4096][1024], W2 bf16 [1024][4096] (out_features x in_features), both
  *        device-resident and owned by the caller.  The job is a fork/join DAG.
+ * SET_JOB_HOTSPOT         dims = {C, R, K}, 1 <= C, R <= 8192, 1 <= K <= 64.
+ *   in : float T0[R][C] (temperatures) followed by float P[R][C] (watts per cell).
+ *   out: float T[R][C] after K explicit steps of the compact thermal RC grid (die 16 mm x 16 mm
+ *        x 0.5 mm, k = 100 W/(m K), c_v = 1.75e6 J/(m^3 K), T_amb = 80, step a fifth of the
+ *        positivity limit, adiabatic edges), zero pad to 16 bytes, trailer.  A chain of 8
+ *        kernels (K/8 steps each, rounded).
  */
 typedef enum {
   SET_JOB_BLUR_HIST = 1,
   SET_JOB_SAXPY_SCAN_MAX = 2,
   SET_JOB_IMG_SOBEL_HIST = 3,
-  SET_JOB_MLP_LN = 4
+  SET_JOB_MLP_LN = 4,
+  SET_JOB_HOTSPOT = 5
 } set_job_type;
 
-#define SET_NUM_JOB_TYPES 4
+#define SET_NUM_JOB_TYPES 5
 
 /* set_job_desc.flags */
 #define SET_F_NONBLOCK 0x1u /* set_submit returns SET_EAGAIN instead of waiting for queue room */

@@ -28,6 +28,14 @@ constexpr uint32_t kCtlStampOff = 1664;      // stamps mode: {arrive, depart} pe
 constexpr uint32_t kCtlImgBytes = 2048;
 constexpr uint32_t kCtlScanOff = kCtlImgBytes;
 
+constexpr uint32_t kCtlHotOff = 1600;        // hotspot job state {CTAs done} inside the fixed region
+constexpr uint32_t kHotCtlBytes = 64;
+static_assert(kCtlHotOff >= kCtlMlpOff + 64 && kCtlHotOff + kHotCtlBytes <= kCtlStampOff, "control regions overlap");
+constexpr int kHotMaxSide = 8192;
+constexpr int kHotLaunches = 8;              // kernel nodes of every hotspot job
+constexpr int kHotStepsPerLaunch = 8;        // time steps one launch advances (its staged halo)
+constexpr int kHotMaxSteps = kHotLaunches * kHotStepsPerLaunch;
+
 constexpr int kMlpD = 1024;
 constexpr int kMlpF = 4096;
 constexpr int kMlpMaxM = 256;

@@ -20,6 +20,9 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
     case SET_JOB_MLP_LN:
       ok = plan_mlp_ln(in, L, kl, nk);
       break;
+    case SET_JOB_HOTSPOT:
+      ok = plan_hotspot(in, L, kl, nk);
+      break;
     default:
       return false;
   }
@@ -31,6 +34,7 @@ bool plan_job(const JobPlanIn& in, KernelLaunch* kl, int* nk) {
 cudaError_t kernels_init() {
   cudaError_t e = blur_hist_init();
   if (e == cudaSuccess) e = mlp_init();
+  if (e == cudaSuccess) e = hotspot_init();
   return e;
 }
 

@@ -46,7 +46,7 @@ __device__ __forceinline__ void stamp_exit(const Stamp& s) {
 }
 #endif
 
-constexpr int kMaxKernels = 6;
+constexpr int kMaxKernels = 8;
 constexpr size_t kMaxArgBytes = 512;  // room for two 128-byte TMA descriptors
 
 struct KernelLaunch {
@@ -92,6 +92,7 @@ bool plan_blur_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, i
 bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 bool plan_mlp_ln(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
+bool plan_hotspot(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk);
 
 // Batched form planners: fill the host table (L.table_bytes) and the kernel launches of one
 // launch over nb jobs whose block starts at d_block.
@@ -104,6 +105,7 @@ bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
 cudaError_t kernels_init();
 cudaError_t blur_hist_init();
 cudaError_t mlp_init();
+cudaError_t hotspot_init();
 
 template <class A>
 inline void set_args(KernelLaunch& k, const A& a) {

@@ -61,20 +61,22 @@ struct SlotState {
   cudaEvent_t done = nullptr;
 };
 
-// Smallest valid dims of each type: graph templates are built with these and every job
-// overwrites all copy and kernel parameters before its launch.
+// Smallest valid dims of each type: graph templates are built with these, so that a slot sized
+// for any one job of the type holds its template, and every job overwrites all copy and kernel
+// parameters before its launch.
 void template_dims(uint32_t type, uint32_t d[4]) {
   d[0] = d[1] = d[2] = d[3] = 0;
   switch (type) {
     case SET_JOB_BLUR_HIST:
     case SET_JOB_IMG_SOBEL_HIST:
-      d[0] = d[1] = 16;
+      d[0] = d[1] = 1;
       break;
     case SET_JOB_SAXPY_SCAN_MAX:
-      d[0] = 256;
-      break;
     case SET_JOB_MLP_LN:
       d[0] = 1;
+      break;
+    case SET_JOB_HOTSPOT:
+      d[0] = d[1] = d[2] = 1;
       break;
     default:
       break;

@@ -48,6 +48,17 @@ bool job_sizes(uint32_t type, const uint32_t d[4], JobLayout* L) {
       L->persist_bytes = kMlpCtlBytes;
       return true;
     }
+    case SET_JOB_HOTSPOT: {
+      if (d[0] < 1 || d[0] > (uint32_t)kHotMaxSide || d[1] < 1 || d[1] > (uint32_t)kHotMaxSide || d[2] < 1 ||
+          d[2] > (uint32_t)kHotMaxSteps)
+        return false;
+      const size_t cells = (size_t)d[0] * d[1];
+      L->in_bytes = 8 * cells;
+      L->out_bytes = ((4 * cells + 15) & ~size_t(15)) + sizeof(set_trailer);
+      L->scratch_bytes = 4 * cells;  // the other buffer of the launches' ping-pong
+      L->persist_bytes = kHotCtlBytes;
+      return true;
+    }
     default:
       return false;
   }
@@ -64,6 +75,8 @@ size_t control_offset(uint32_t type) {
       return kCtlScanOff;
     case SET_JOB_MLP_LN:
       return kCtlMlpOff;
+    case SET_JOB_HOTSPOT:
+      return kCtlHotOff;
     default:
       return kCtlImgOff;
   }

@@ -194,5 +194,29 @@ def serve_jobs(lam, n, img_cap=None):
     return jobs, (t * 1e9).astype(np.uint64)
 
 
+def hot_job(j, R=datagen.HOT_SIDE, C=datagen.HOT_SIDE, K=datagen.HOT_STEPS, **kw):
+    x = datagen.hot_job(j, R, C)
+    return Job(S().SET_JOB_HOTSPOT, (C, R, K), x, **kw)
+
+
+HOT_RTOL = 1e-5  # |T_gpu - T| <= 1e-5 |T| per cell (fp32 steps vs the fp64 oracle)
+
+
+def check_hot(job):
+    import oracle
+    C, R, K = job.dims
+    x = job.payload
+    ref = oracle.hotspot(x[:R * C].reshape(R, C), x[R * C:].reshape(R, C), K)
+    o = job.out()
+    got = o[:4 * R * C].view(np.float32).reshape(R, C).astype(np.float64)
+    assert np.isfinite(got).all(), "non-finite temperature"
+    rel = np.abs(got - ref) / np.abs(ref)
+    worst = float(rel.max())
+    assert worst <= HOT_RTOL, f"{C}x{R}, K={K}: worst relative error {worst:.3e} at {np.unravel_index(rel.argmax(), rel.shape)}"
+    off = (4 * R * C + 15) & ~15
+    assert not o[4 * R * C:off].any(), "pad bytes not zero"
+    return worst
+
+
 def check_any(job):
-    {1: check_blur, 2: check_scan, 3: check_img, 4: check_mlp}[job.type](job)
+    {1: check_blur, 2: check_scan, 3: check_img, 4: check_mlp, 5: check_hot}[job.type](job)

@@ -71,8 +71,11 @@ def test_documented_payload_sizes():
     assert S.set_job_out_bytes(3, d(641, 3)) == 1936 + 1024 + 16
     assert S.set_job_in_bytes(4, d(7)) == 7 * 1024 * 2
     assert S.set_job_out_bytes(4, d(7)) == 7 * 1024 * 4 + 16
+    assert S.set_job_in_bytes(5, d(512, 512, 64)) == 2 * 512 * 512 * 4  # T0 then P
+    assert S.set_job_out_bytes(5, d(512, 512, 64)) == 512 * 512 * 4 + 16
+    assert S.set_job_out_bytes(5, d(3, 5, 1)) == 64 + 16  # 60 bytes padded to 64
     for t, dims in [(1, d(0, 5)), (1, d(2049, 5)), (2, d(0)), (2, d(1 << 27)), (3, d(4097, 2)), (4, d(0)),
-                    (4, d(257)), (9, d(1, 1))]:
+                    (4, d(257)), (5, d(16, 16, 0)), (5, d(16, 16, 65)), (5, d(8193, 2, 1)), (9, d(1, 1))]:
         assert S.set_job_in_bytes(t, dims) == 0 and S.set_job_out_bytes(t, dims) == 0
     assert S.set_job_scratch_bytes(2, d(65536)) == 512  # 64-byte header + 16 tiles x 16 bytes, aligned
     sb = S.set_job_slot_bytes(2, d(65536))

@@ -144,3 +144,17 @@ def test_polled_completion_destroy_with_jobs_in_flight(cb_every):
         assert j.status.value == 0, (k, j.status.value)
         check_scan(j)
     check_trailers(jobs)
+
+
+@pytest.mark.parametrize("kind", ["blur", "scan", "img"])
+def test_smallest_job_in_a_slot_sized_for_it(kind):
+    # the graph template of every type fits a slot sized by set_job_slot_bytes for its smallest job
+    from gpu_util import check_img, img_job
+    s = S()
+    job = {"blur": lambda: blur_job(1, W=1, H=1), "scan": lambda: scan_job(2, n=1),
+           "img": lambda: img_job(3, dims=(1, 1))}[kind]()
+    slot = s.set_job_slot_bytes(job.type, s.dims4(*job.dims))
+    st = run_jobs([job], num_streams=1, num_workers=1, ring_depth=1, slot_bytes=slot)
+    assert st["completed"] == 1 and st["failed"] == 0
+    {"blur": check_blur, "scan": check_scan, "img": check_img}[kind](job)
+    check_trailers([job])
