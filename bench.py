@@ -616,6 +616,43 @@ def _baseline(S, cfg, kind, descs, n):
         S.set_destroy(ctx)
 
 
+TRACE_FIELDS = ("kernels", "memcpys", "span_us", "kernel_busy_us", "copy_busy_us", "idle_frac",
+                "mean_kernel_gap_us", "max_kernel_gap_us", "top_kernel_mean_us")
+
+
+def _traces(S, cfg, descs, n):
+    """One CUPTI-traced (untimed) step of SET and one of the batch-synchronous baseline on the same
+    jobs and slots: device-timeline gaps (Sec. 3.2, Eq. 2-4)."""
+    out = {}
+    ctx = S.create(S.default_config(**cfg))
+    try:
+        run_step(S, ctx, descs, n)
+        tr = S.set_trace_summary()
+        if S.set_trace_start() == S.SET_OK:
+            run_step(S, ctx, descs, n)
+            S.set_trace_stop(ctypes.byref(tr))
+            out["set"] = {f: getattr(tr, f) for f in TRACE_FIELDS}
+        if S.set_trace_start() == S.SET_OK:
+            st = S.set_stats_t()
+            S.set_run_baseline(ctx, S.SET_BASE_BATCH_SYNC, descs, n, ctypes.byref(st))
+            S.set_trace_stop(ctypes.byref(tr))
+            out["batch_sync_graph"] = {f: getattr(tr, f) for f in TRACE_FIELDS}
+    finally:
+        S.set_destroy(ctx)
+    return out
+
+
+def _copy_bound(S, js, n, streams, e2e_jobs_per_s):
+    """Copy-engine bound of a workload (jobs/s) from pinned copy rates at its mean job sizes, and
+    the measured end-to-end rate as a fraction of it."""
+    mi, mo = js.bytes_in // n, js.bytes_out // n
+    rates = copy_rates(S, mi, mo, streams, reps=1024)
+    t = max(js.bytes_in / (rates["h2d_gbs"] * 1e9), js.bytes_out / (rates["d2h_gbs"] * 1e9),
+            (js.bytes_in + js.bytes_out) / (rates["bidir_total_gbs"] * 1e9))
+    return {"copy_rates_gbs": rates, "mean_in_bytes": mi, "mean_out_bytes": mo, "bound_jobs_per_s": n / t,
+            "e2e_frac_of_bound": e2e_jobs_per_s * t / n}
+
+
 def run_workload(args, d: Dist):
     """One JSON line per workload: SET forms against the batch-synchronous graph baseline."""
     import paper_2606_05495_gb300 as S
@@ -632,12 +669,16 @@ def run_workload(args, d: Dist):
         js = JobSet(S, 1, range(n), device_copy=True)
         cfg = dict(common, num_streams=2, ring_depth=4, slot_bytes=js.slot_bytes(S))
         line["config"] = {"jobs_per_step": n, "side": 256, "streams": 2, "note": "64-job configuration x 200"}
-        line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
-        line["set_per_job_callbacks"] = _rate(S, dict(cfg, cb_every=1), js.descs, n, args, d)
-        line["set_device_resident"] = _rate(S, dict(cfg, cb_every=8, io_mode=S.SET_IO_DEVICE), js.descs_dev, n, args, d)
-        line["set_16_streams"] = _rate(S, dict(cfg, cb_every=8, num_streams=16), js.descs, n, args, d)
+        polled = dict(cfg, cb_mode=3, num_workers=2)
+        line["set"] = _rate(S, polled, js.descs, n, args, d, clocks)
+        line["set_host_callbacks_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
+        line["set_host_callbacks_per_job"] = _rate(S, dict(cfg, cb_every=1), js.descs, n, args, d)
+        line["set_device_resident"] = _rate(S, dict(polled, io_mode=S.SET_IO_DEVICE), js.descs_dev, n, args, d)
+        line["set_16_streams"] = _rate(S, dict(polled, num_streams=16), js.descs, n, args, d)
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
+        line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"])
+        line["trace"] = _traces(S, polled, js.descs, n)
     elif args.workload in ("img", "mlp"):
         kind = 3 if args.workload == "img" else 4
         n = min(args.jobs, 2000)
@@ -646,9 +687,11 @@ def run_workload(args, d: Dist):
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=sb)
         line["config"] = {"jobs": n, "sample_of": 10000 if kind == 3 else 2000, "streams": 16,
                           "in_bytes": js.bytes_in, "out_bytes": js.bytes_out}
-        line["set_per_job"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
+        polled = dict(cfg, cb_mode=3, num_workers=2)
+        line["set_per_job"] = _rate(S, polled, js.descs, n, args, d, clocks)
+        line["set_per_job_host_callbacks"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
         if kind == 3:
-            line["set_per_stage_graphs"] = _rate(S, dict(cfg, cb_every=8, img_fused=0), js.descs, n, args, d)
+            line["set_per_stage_graphs"] = _rate(S, dict(polled, img_fused=0), js.descs, n, args, d)
         # batched form: autotuned jobs per launch (and tile / CTAs per SM for images) in an 8 GiB arena
         bcfg = dict(cfg, cb_every=2, ring_depth=2, batch_max=16, arena_bytes=8 << 30, slot_bytes=1 << 30)
         ctx = S.create(S.default_config(**bcfg))
@@ -660,6 +703,9 @@ def run_workload(args, d: Dist):
         line["set_batched"] = {"jobs_per_s": n / (ms * 1e-3), "ms_per_step": ms, "p99_us": st["p99_us"],
                                "failed": st["failed"], "autotune": tune.as_dict()}
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
+        best = max(line["set_per_job"]["jobs_per_s"], line["set_batched"]["jobs_per_s"])
+        line["pipeline"] = _copy_bound(S, js, n, 16, best)
+        line["trace"] = _traces(S, polled, js.descs, n)
         if kind == 4:
             flop = 2.0 * js.rows() * 1024 * 4096 * 2
             line["gemm_tflops_e2e"] = {k: flop / (line[k]["ms_per_step"] * 1e-3) / 1e12
@@ -669,6 +715,15 @@ def run_workload(args, d: Dist):
         n = min(args.jobs, 1000)
         js = JobSet(S, 5, range(n), device_copy=True)
         C, R, K = js.dims[0]
+        if args.kernel_only:  # profiling: the jobs' kernel chains alone, then exit
+            scratch = t.zeros(S.set_job_scratch_bytes(5, S.dims4(C, R, K)), dtype=t.uint8, device="cuda")
+            for k in range(args.kernel_only):
+                dd = js.descs_dev[k % n]
+                S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0,
+                                         t.cuda.current_stream().cuda_stream), "set_launch_job")
+            t.cuda.synchronize()
+            print(json.dumps({"kernel_only": "hotspot_kernel", "jobs": args.kernel_only, "launches": 8 * args.kernel_only}))
+            return
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=js.slot_bytes(S))
         line["config"] = {"jobs": n, "grid": [R, C], "steps": K, "streams": 16, "in_bytes": js.bytes_in,
                           "out_bytes": js.bytes_out, "l2": "inputs > L2 (no flush needed)"}
@@ -678,6 +733,8 @@ def run_workload(args, d: Dist):
                                             js.descs_dev, n, args, d, clocks)
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
+        line["pipeline"] = _copy_bound(S, js, n, 16, line["set_polled_2_workers"]["jobs_per_s"])
+        line["trace"] = _traces(S, dict(cfg, cb_mode=3, num_workers=2), js.descs, n)
         # the kernel chain alone: CUDA events around each job's 8 launches on one stream
         st = t.cuda.Stream()
         scratch = t.zeros(S.set_job_scratch_bytes(5, S.dims4(C, R, K)), dtype=t.uint8, device="cuda")

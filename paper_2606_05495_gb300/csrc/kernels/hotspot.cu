@@ -11,8 +11,10 @@
 // stages the (64 + 2h) x (64 + 2h) window of T and P around its 64 x 64 output tile (h = 8,
 // 16-byte cp.async copies when rows allow), turns P into q = dt/Cap P + dt Gz/Cap T_amb, runs the
 // steps in shared memory over a region that shrinks by one cell per step (a cell's new value needs
-// its neighbours' old values) and writes its tile.  Thread t owns column t % 80 of one of four
-// 20-row strips and walks down it with the column's north / centre / south values in registers.  Neighbour reads clamp to the die, so staged cells outside it are never read.  A job
+// its neighbours' old values) and writes its tile.  Thread t owns a group of four columns of one
+// of sixteen 5-row strips and walks down it with the group's north / centre / south rows in
+// float4 registers (two 128-bit and two 32-bit shared loads per four cells).  CTAs whose window
+// lies inside the die skip the edge selects.  Neighbour reads clamp to the die, so staged cells outside it are never read.  A job
 // is kHotLaunches launches that alternate between the slot's scratch buffer and the output; the
 // last CTA of the last launch writes the zero pad and the trailer.
 #include "stages.h"
@@ -23,10 +25,11 @@ namespace {
 constexpr int kTile = 64;
 constexpr int kHalo = kHotStepsPerLaunch;
 constexpr int kS = kTile + 2 * kHalo;  // staged window side
-constexpr int kStrips = 4;             // row strips of the window; a thread per (column, strip)
+constexpr int kGroups = kS / 4;        // four-column groups across the window
+constexpr int kStrips = 16;            // row strips of the window; a thread per (group, strip)
 constexpr int kStripRows = kS / kStrips;
-constexpr int kThreads = kS * kStrips;
-static_assert(kS % kStrips == 0, "strips tile the window");
+constexpr int kThreads = kGroups * kStrips;
+static_assert(kS % kStrips == 0 && kS % 4 == 0, "strips and groups tile the window");
 constexpr unsigned kSmemBytes = 3u * kS * kS * sizeof(float);  // two T buffers and q
 static_assert(kS % 4 == 0 && kHalo % 4 == 0, "16-byte staging needs 4-cell aligned windows");
 
@@ -75,6 +78,50 @@ __device__ void stage(float* dst, const float* __restrict__ src, int C, int R, i
   }
 }
 
+// One explicit step over this thread's rows of the region [s, kS - s)^2.  Groups that reach into
+// the region compute all four columns: the cells outside it are never read again.  EDGE: the
+// window touches the die's border, so neighbours clamp to the die (adiabatic edges).
+template <bool EDGE>
+__device__ __forceinline__ void step(const float* __restrict__ cur, float* __restrict__ nxt, const float* __restrict__ qs,
+                                     int s, int grp, int g, int gx0, int gy0, int C, int R, float cx, float cy,
+                                     float cz) {
+  const int c0 = 4 * grp;
+  const int r0 = max(g * kStripRows, s), r1 = min((g + 1) * kStripRows, kS - s);
+  if (c0 + 3 < s || c0 >= kS - s || r0 >= r1) return;
+  bool west[4], east[4];  // the neighbour exists on the die
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    west[k] = !EDGE || gx0 + c0 + k > 0;
+    east[k] = !EDGE || gx0 + c0 + k < C - 1;
+  }
+  const float4* cur4 = reinterpret_cast<const float4*>(cur);
+  float4 up = cur4[((r0 - 1) * kS + c0) / 4], mid = cur4[(r0 * kS + c0) / 4];
+#pragma unroll 5
+  for (int r = r0; r < r1; ++r) {
+    const int i = r * kS + c0;  // in-bounds: 1 <= r <= kS - 2, and i + 4 <= (r + 1) * kS
+    const float4 dn = cur4[(i + kS) / 4];
+    const float4 q = reinterpret_cast<const float4*>(qs)[i / 4];
+    const float w = cur[i - 1], e = cur[i + 4];  // c0 = kS - 4: the next row's first cell, never in a region
+    const bool north = !EDGE || gy0 + r > 0, south = !EDGE || gy0 + r < R - 1;
+    const float m[4] = {mid.x, mid.y, mid.z, mid.w}, u[4] = {up.x, up.y, up.z, up.w}, d[4] = {dn.x, dn.y, dn.z, dn.w};
+    const float qq[4] = {q.x, q.y, q.z, q.w};
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float t = m[k];
+      const float tn = north ? u[k] : t, ts = south ? d[k] : t;
+      const float tw = west[k] ? (k == 0 ? w : m[k - 1]) : t, te = east[k] ? (k == 3 ? e : m[k + 1]) : t;
+      float acc = fmaf(cy, (tn + ts) - 2.f * t, qq[k]);
+      acc = fmaf(cx, (tw + te) - 2.f * t, acc);
+      acc = fmaf(-cz, t, acc);
+      o[k] = t + acc;
+    }
+    reinterpret_cast<float4*>(nxt)[i / 4] = make_float4(o[0], o[1], o[2], o[3]);
+    up = mid;
+    mid = dn;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) hotspot_kernel(const HotArgs a) {
   extern __shared__ __align__(16) float sm[];
   float* cur = sm;
@@ -90,37 +137,22 @@ __global__ void __launch_bounds__(kThreads, 2) hotspot_kernel(const HotArgs a) {
   stage(qs, a.p, C, R, gx0, gy0, vec);
   cp_async_wait_all();
   __syncthreads();
-  const float cx = a.cx, cy = a.cy, cz = a.cz;
   {
     const float cp = a.cp, czt = a.cz * a.tamb;
-    for (int i = threadIdx.x; i < kS * kS; i += kThreads) qs[i] = fmaf(cp, qs[i], czt);  // cells off the die: unused
+    float4* q4 = reinterpret_cast<float4*>(qs);
+    for (int i = threadIdx.x; i < kS * kS / 4; i += kThreads) {  // cells off the die: unused
+      const float4 p = q4[i];
+      q4[i] = make_float4(fmaf(cp, p.x, czt), fmaf(cp, p.y, czt), fmaf(cp, p.z, czt), fmaf(cp, p.w, czt));
+    }
   }
   __syncthreads();
-  const int col = threadIdx.x % kS, g = threadIdx.x / kS;
-  const int gxc = gx0 + col;
-  const bool col_in = gxc >= 0 && gxc < C, has_w = gxc > 0, has_e = gxc < C - 1;
+  const int grp = threadIdx.x % kGroups, g = threadIdx.x / kGroups;
+  const bool edge = gx0 < 0 || gy0 < 0 || gx0 + kS > C || gy0 + kS > R;
   for (int s = 1; s <= (int)a.steps; ++s) {
-    // this step's region is rows and columns [s, kS - s): every value it reads was updated last step
-    const int r0 = max(g * kStripRows, s), r1 = min((g + 1) * kStripRows, kS - s);
-    if (col_in && col >= s && col < kS - s && r0 < r1) {
-      float up = cur[(r0 - 1) * kS + col], mid = cur[r0 * kS + col];
-#pragma unroll 4
-      for (int r = r0; r < r1; ++r) {
-        const int i = r * kS + col;
-        const float dn = cur[i + kS];
-        const int gy = gy0 + r;
-        if (gy >= 0 && gy < R) {
-          const float tn = gy > 0 ? up : mid, ts = gy < R - 1 ? dn : mid;  // adiabatic edges
-          const float tw = has_w ? cur[i - 1] : mid, te = has_e ? cur[i + 1] : mid;
-          float acc = fmaf(cy, (tn + ts) - 2.f * mid, qs[i]);
-          acc = fmaf(cx, (tw + te) - 2.f * mid, acc);
-          acc = fmaf(-cz, mid, acc);
-          nxt[i] = mid + acc;
-        }
-        up = mid;
-        mid = dn;
-      }
-    }
+    if (edge)
+      step<true>(cur, nxt, qs, s, grp, g, gx0, gy0, C, R, a.cx, a.cy, a.cz);
+    else
+      step<false>(cur, nxt, qs, s, grp, g, gx0, gy0, C, R, a.cx, a.cy, a.cz);
     __syncthreads();
     float* sw = cur;
     cur = nxt;
