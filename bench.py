@@ -653,6 +653,19 @@ def _copy_bound(S, js, n, streams, e2e_jobs_per_s):
             "e2e_frac_of_bound": e2e_jobs_per_s * t / n}
 
 
+def _kernel_only(S, js, n, launches):
+    """Profiling: the stage kernels of `launches` resident jobs alone on one stream, then exit."""
+    t = _torch()
+    sb = max(S.set_job_scratch_bytes(js.kind, S.dims4(*dd)) for dd in js.dims)
+    scratch = t.zeros(max(sb, 256), dtype=t.uint8, device="cuda")
+    st = t.cuda.current_stream().cuda_stream
+    for k in range(launches):
+        dd = js.descs_dev[k % n]
+        S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st), "set_launch_job")
+    t.cuda.synchronize()
+    print(json.dumps({"kernel_only": js.kind, "jobs": launches}), flush=True)
+
+
 def run_workload(args, d: Dist):
     """One JSON line per workload: SET forms against the batch-synchronous graph baseline."""
     import paper_2606_05495_gb300 as S
@@ -667,6 +680,8 @@ def run_workload(args, d: Dist):
         # over (12,800 distinct jobs, each with its own input and output)
         n = 64 * 200
         js = JobSet(S, 1, range(n), device_copy=True)
+        if args.kernel_only:
+            return _kernel_only(S, js, n, args.kernel_only)
         cfg = dict(common, num_streams=2, ring_depth=4, slot_bytes=js.slot_bytes(S))
         line["config"] = {"jobs_per_step": n, "side": 256, "streams": 2, "note": "64-job configuration x 200"}
         polled = dict(cfg, cb_mode=3, num_workers=2)
@@ -682,7 +697,9 @@ def run_workload(args, d: Dist):
     elif args.workload in ("img", "mlp"):
         kind = 3 if args.workload == "img" else 4
         n = min(args.jobs, 2000)
-        js = JobSet(S, kind, range(n))
+        js = JobSet(S, kind, range(n), device_copy=bool(args.kernel_only))
+        if args.kernel_only:
+            return _kernel_only(S, js, n, args.kernel_only)
         sb = js.slot_bytes(S)
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=sb)
         line["config"] = {"jobs": n, "sample_of": 10000 if kind == 3 else 2000, "streams": 16,
@@ -715,15 +732,8 @@ def run_workload(args, d: Dist):
         n = min(args.jobs, 1000)
         js = JobSet(S, 5, range(n), device_copy=True)
         C, R, K = js.dims[0]
-        if args.kernel_only:  # profiling: the jobs' kernel chains alone, then exit
-            scratch = t.zeros(S.set_job_scratch_bytes(5, S.dims4(C, R, K)), dtype=t.uint8, device="cuda")
-            for k in range(args.kernel_only):
-                dd = js.descs_dev[k % n]
-                S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0,
-                                         t.cuda.current_stream().cuda_stream), "set_launch_job")
-            t.cuda.synchronize()
-            print(json.dumps({"kernel_only": "hotspot_kernel", "jobs": args.kernel_only, "launches": 8 * args.kernel_only}))
-            return
+        if args.kernel_only:
+            return _kernel_only(S, js, n, args.kernel_only)
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=js.slot_bytes(S))
         line["config"] = {"jobs": n, "grid": [R, C], "steps": K, "streams": 16, "in_bytes": js.bytes_in,
                           "out_bytes": js.bytes_out, "l2": "inputs > L2 (no flush needed)"}

@@ -26,7 +26,7 @@ CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_
               "kernels/mlp_ln.cu", "kernels/hotspot.cu", "kernels/plan.cu"]
 CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp",
                "runtime/trace.cpp"]
-HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "runtime/executor.h", "runtime/sync.h",
+HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "kernels/cp_async.cuh", "runtime/executor.h", "runtime/sync.h",
            "runtime/layout.h", "runtime/thread_error.h"]
 
 INCLUDES = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include")]

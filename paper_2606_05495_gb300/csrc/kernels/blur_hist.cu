@@ -2,12 +2,13 @@
 // the 256-bin histogram of the blurred image.
 //
 // One thread-block cluster of 8 CTAs per job.  Each CTA owns a band of rows, stages it (plus a
-// one-row halo, rows clamped) in shared memory with 16-byte loads, writes 16 output pixels per
+// one-row halo, rows clamped) in shared memory with 16-byte cp.async, writes 16 output pixels per
 // work item with one 16-byte store, and counts them in per-warp privatised shared histograms.
 // The 8 CTA histograms are summed through distributed shared memory (each CTA reduces 32 bins
 // across the cluster), so the job needs no global atomics, no zeroing pass and no scratch.
 #include <cooperative_groups.h>
 
+#include "cp_async.cuh"
 #include "stages.h"
 
 namespace cg = cooperative_groups;
@@ -54,14 +55,14 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
 
   for (int cy = y0; cy < y1; cy += kChunkRows) {
     const int ny = min(kChunkRows, y1 - cy);
-    if (vec) {
+    if (vec) {  // every 16-byte copy of the band in flight at once
       const int vpr = W >> 4;
       for (int i = tid; i < (ny + 2) * vpr; i += kThreads) {
         const int r = i / vpr, c = i - r * vpr;
         const int sy = min(max(cy - 1 + r, 0), H - 1);
-        reinterpret_cast<uint4*>(tile + r * pitch)[c] =
-            __ldg(reinterpret_cast<const uint4*>(a.in + (size_t)sy * W) + c);
+        cp_async16(tile + r * pitch + 16 * c, a.in + (size_t)sy * W + 16 * c);
       }
+      cp_async_wait_all();
     } else {
       for (int i = tid; i < (ny + 2) * W; i += kThreads) {
         const int r = i / W, c = i - r * W;

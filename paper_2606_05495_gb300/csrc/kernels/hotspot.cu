@@ -17,6 +17,7 @@
 // lies inside the die skip the edge selects.  Neighbour reads clamp to the die, so staged cells outside it are never read.  A job
 // is kHotLaunches launches that alternate between the slot's scratch buffer and the output; the
 // last CTA of the last launch writes the zero pad and the trailer.
+#include "cp_async.cuh"
 #include "stages.h"
 
 namespace setk {
@@ -48,15 +49,6 @@ struct HotArgs {
   uint32_t slot_gen;
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // dst[r][c] = src[gy0 + r][gx0 + c] for the window cells inside the die; the others are left.
 __device__ void stage(float* dst, const float* __restrict__ src, int C, int R, int gx0, int gy0, bool vec) {

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "cp_async.cuh"
 #include "stages.h"
 
 namespace setk {
@@ -102,11 +103,6 @@ __device__ void stage_gray(uint8_t (*g_s)[P], const uint8_t* __restrict__ rgb, i
   }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Words of 16 bytes that one staged RGB row run occupies in shared memory: up to 15 bytes of lead
 // (the run starts anywhere inside its first 16-byte word) plus 3 * GC bytes, rounded up.
