@@ -12,6 +12,7 @@
 //   SET_SIM_DROP_EVERY=k     every k-th launch never completes (a lost callback)
 //   SET_SIM_BADGEN_EVERY=k   every k-th launch writes a wrong slot generation (stale slot)
 //   SET_SIM_FAIL_EVERY=k     every k-th launch fails with SET_ECUDA at launch time
+//   SET_SIM_SLOW_LANE=i,f    lane i's delays are f times longer (a lane that falls behind)
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -44,6 +45,7 @@ class SimDevice final : public Device {
     drop_ = env_long("SET_SIM_DROP_EVERY", 0);
     badgen_ = env_long("SET_SIM_BADGEN_EVERY", 0);
     fail_ = env_long("SET_SIM_FAIL_EVERY", 0);
+    if (const char* sl = std::getenv("SET_SIM_SLOW_LANE")) std::sscanf(sl, "%ld,%ld", &slow_lane_, &slow_factor_);
     for (auto& s : slots) s.bytes = cfg.slot_bytes;
     dropped_.assign(slots.size(), 0);
     // arena mode: host bytes stand in for the device range (the simulation never touches them)
@@ -152,7 +154,7 @@ class SimDevice final : public Device {
           cb_cv_.notify_one();
         }
       } else {
-        const long us = lo_ + (long)(rng() % (uint64_t)(hi_ - lo_ + 1));
+        const long us = (lo_ + (long)(rng() % (uint64_t)(hi_ - lo_ + 1))) * (i == slow_lane_ ? slow_factor_ : 1);
         std::this_thread::sleep_for(std::chrono::microseconds(us));
         auto write = [&](const JobRec& j) {
           set_trailer t;
@@ -204,7 +206,7 @@ class SimDevice final : public Device {
     if (cb_th_.joinable()) cb_th_.join();
   }
 
-  long lo_ = 5, hi_ = 50, drop_ = 0, badgen_ = 0, fail_ = 0;
+  long lo_ = 5, hi_ = 50, drop_ = 0, badgen_ = 0, fail_ = 0, slow_lane_ = -1, slow_factor_ = 1;
   std::vector<uint8_t> arena_;
   std::vector<char> dropped_;  // per slot: its last job "lost" its callback
   std::atomic<uint64_t> launches_{0};

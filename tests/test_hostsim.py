@@ -15,7 +15,7 @@ import pytest
 import hostsim_util
 import paper_2606_05495_gb300 as B  # ctypes structs only; calls below go to the simulation library
 
-SIM_ENV = ("SET_SIM_DELAY_US", "SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY")
+SIM_ENV = ("SET_SIM_DELAY_US", "SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY", "SET_SIM_SLOW_LANE")
 
 
 @pytest.fixture
@@ -94,11 +94,42 @@ def test_every_job_completes_exactly_once(sim):
     assert sim.set_wait_all(ctx, 30_000_000) == 0
     st = stats(sim, ctx)
     sim.set_destroy(ctx)
-    assert st.submitted == st.completed == n and st.failed == 0 and st.canary_errors == 0
+    assert st.submitted == st.completed == n and st.failed == 0 and st.canary_errors == 0, st.as_dict()
     assert np.array_equal(np.sort(jobs.trailer_ids()), np.arange(first, first + n, dtype=np.uint64))
     assert all(s == 0 for s in jobs.status)
     assert st.p50_us <= st.p99_us <= st.max_us * 1.02 + 1
-    assert st.steals > 0  # with uneven delays some lane always runs dry first
+
+
+def test_idle_lanes_steal_from_a_lane_that_falls_behind(sim):
+    # Algorithm 2: a slot whose lane queue is empty takes the next job of lane (w + k) mod b.
+    # Lane 0 runs 40x slower, so the other lanes empty their queues while lane 0 still holds jobs.
+    os.environ["SET_SIM_DELAY_US"] = "20,30"
+    os.environ["SET_SIM_SLOW_LANE"] = "0,40"
+    n = 400
+    jobs = Jobs(n)
+    ctx = create(sim, num_streams=4, num_workers=1, ring_depth=1, queue_capacity=1000)
+    rc, first, done = submit_all(sim, ctx, jobs, n)
+    assert rc == 0 and done == n
+    assert sim.set_wait_all(ctx, 60_000_000) == 0
+    st = stats(sim, ctx)
+    sim.set_destroy(ctx)
+    assert st.completed == n and st.failed == 0 and st.canary_errors == 0
+    assert np.array_equal(np.sort(jobs.trailer_ids()), np.arange(first, first + n, dtype=np.uint64))
+    assert st.steals > 0
+
+
+def test_no_steals_without_stealing(sim):
+    os.environ["SET_SIM_DELAY_US"] = "20,30"
+    os.environ["SET_SIM_SLOW_LANE"] = "0,40"
+    n = 200
+    jobs = Jobs(n)
+    ctx = create(sim, num_streams=4, num_workers=1, ring_depth=1, queue_capacity=1000, steal=0)
+    rc, first, done = submit_all(sim, ctx, jobs, n)
+    assert rc == 0 and done == n
+    assert sim.set_wait_all(ctx, 60_000_000) == 0
+    st = stats(sim, ctx)
+    sim.set_destroy(ctx)
+    assert st.completed == n and st.failed == 0 and st.steals == 0
 
 
 @pytest.mark.parametrize("every,lanes,ring", [(2, 3, 2), (4, 2, 1), (8, 5, 3), (3, 1, 1)])
