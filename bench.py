@@ -455,6 +455,12 @@ def run_set(args, d: Dist):
             traces["batch_sync_graph"] = tr.as_dict()
     S.set_destroy(ctx)
 
+    # the same pinned host buffers read and written by the kernels over the host link (no copy
+    # nodes; SET_IO_MAPPED)
+    ctxm = S.create(S.default_config(io_mode=S.SET_IO_MAPPED, **cfg))
+    ms_map, st_map = timed(S, ctxm, w.descs_host, nj, args, d)
+    S.set_destroy(ctxm)
+
     k_mean_us, k_med_us = kernel_time(S, w)
     rates = copy_rates(S, JOB_IN, JOB_OUT, args.streams)
     world = d.world
@@ -495,6 +501,11 @@ def run_set(args, d: Dist):
                                        "mean_launch_us": v[1]["mean_launch_us"]} for k, v in host_cb.items()},
                 "note": "completion by polled events (cb_mode 3); host_callbacks: cudaLaunchHostFunc on a "
                         "callback stream (cb_mode 0), one dispatch thread"},
+        "e2e_mapped": {"value": world * nj / (ms_map * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
+                       "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_map, "p50_us": st_map["p50_us"],
+                       "p99_us": st_map["p99_us"],
+                       "note": "SET_IO_MAPPED: the same pinned host buffers, read and written by the kernels "
+                               "over NVLink-C2C; the job graphs have no copy nodes"},
         "gpu_launches": args.steps * nj * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
@@ -694,6 +705,8 @@ def run_workload(args, d: Dist):
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
         line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
+        # kernels reading and writing the pinned buffers over NVLink-C2C, no copy nodes
+        line["set_mapped_io"] = _rate(S, dict(polled, io_mode=S.SET_IO_MAPPED), js.descs, n, args, d)
     elif args.workload in ("img", "mlp"):
         kind = 3 if args.workload == "img" else 4
         n = min(args.jobs, 2000)

@@ -120,8 +120,17 @@ typedef struct {
   volatile int32_t* status; /* optional: set to a set_status when the job completes */
 } set_job_desc;
 
-/* Input / output placement of every job of a context. */
-typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1 } set_io_mode;
+/* Input / output placement of every job of a context.
+ *   SET_IO_HOST    in / out are page-locked host buffers, moved by the graph's H2D / D2H copy
+ *                  nodes (the paper's job: H2D -> kernels -> D2H).
+ *   SET_IO_DEVICE  in / out are device buffers of the context's GPU (device-to-device copies).
+ *   SET_IO_MAPPED  in / out are page-locked host buffers mapped into the GPU's address space
+ *                  (cudaHostAlloc, a pinned torch tensor); the stage kernels read and write them
+ *                  directly over the host link, so a job's graph has no copy nodes.  An addition
+ *                  for hosts coherently attached to the GPU (NVLink-C2C); not for MLP jobs,
+ *                  whose x feeds TMA loads (SET_EINVAL), nor for the batched form or baselines.
+ *                  Buffers the device cannot address are rejected at submit with SET_EINVAL. */
+typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1, SET_IO_MAPPED = 2 } set_io_mode;
 
 typedef struct {
   int num_streams;     /* lanes b (paper's workers), >= 1 */

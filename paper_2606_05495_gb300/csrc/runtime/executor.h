@@ -73,6 +73,8 @@ class Device {
   virtual uint8_t* arena_base() = 0;
   // True if graphs for jobs of this type were instantiated.
   virtual bool supports(uint32_t type) const = 0;
+  // SET_IO_MAPPED: true if the device can address the host buffer p directly.
+  virtual bool io_accessible(const void* p) const = 0;
   // Autotuner of the batched form (the context's workers are idle): picks jobs per launch (<=
   // max_batch) and the image kernel's tile / CTAs per SM, applies them to later launches.
   virtual set_status autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
