@@ -455,6 +455,11 @@ def run_set(args, d: Dist):
             traces["batch_sync_graph"] = tr.as_dict()
     S.set_destroy(ctx)
 
+    # UpdateGraphParams at submit (the submitting thread binds free slots) instead of at dispatch
+    ctxb = S.create(S.default_config(io_mode=S.SET_IO_HOST, bind_at_submit=1, **cfg))
+    ms_bind, st_bind = timed(S, ctxb, w.descs_host, nj, args, d)
+    S.set_destroy(ctxb)
+
     # the same pinned host buffers read and written by the kernels over the host link (no copy
     # nodes; SET_IO_MAPPED)
     ctxm = S.create(S.default_config(io_mode=S.SET_IO_MAPPED, **cfg))
@@ -501,6 +506,10 @@ def run_set(args, d: Dist):
                                        "mean_launch_us": v[1]["mean_launch_us"]} for k, v in host_cb.items()},
                 "note": "completion by polled events (cb_mode 3); host_callbacks: cudaLaunchHostFunc on a "
                         "callback stream (cb_mode 0), one dispatch thread"},
+        "e2e_bind_at_submit": {"value": world * nj / (ms_bind * 1e-3), "unit": UNIT, "ms_per_step": ms_bind,
+                               "p99_us": st_bind["p99_us"], "mean_update_us": st_bind["mean_update_us"],
+                               "mean_launch_us": st_bind["mean_launch_us"],
+                               "note": "UpdateGraphParams on the submitting thread (set_config.bind_at_submit)"},
         "e2e_mapped": {"value": world * nj / (ms_map * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
                        "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_map, "p50_us": st_map["p50_us"],
                        "p99_us": st_map["p99_us"],

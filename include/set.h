@@ -171,6 +171,12 @@ typedef struct {
                           size (buddy blocks, 64 KiB minimum) and freed by its completion callback,
                           so jobs are admitted by free memory; slots then hold only the kernels'
                           control state and slot_bytes only bounds the largest job */
+  int bind_at_submit;  /* 0 (default): UpdateGraphParams at dispatch (a dispatch thread binds the job
+                          to the slot it pops); 1: at submit, as Algorithm 1 lists it: the
+                          submitting thread takes a free slot if one is ready, rebinds the slot's
+                          graph to the job and queues it bound, so dispatch threads only launch
+                          (jobs that find no free slot are bound at dispatch).  Not with
+                          arena_bytes or batch_max > 1. */
 } set_config;
 
 typedef struct {

@@ -107,6 +107,8 @@ class CudaDevice final : public Device {
 
   set_status init(const set_config& cfg, std::vector<Slot>& slots, std::string* err) override;
   set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override;
+  set_status prepare(Slot& s, LaunchCost* cost, std::string* err) override;
+  set_status launch_bound(Slot& s, bool callback, LaunchCost* cost, std::string* err) override;
   set_status launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override;
   set_status autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
                       std::string* err) override;
@@ -462,17 +464,36 @@ set_status CudaDevice::attach_callback(Slot& s, std::string* err) {
 }
 
 set_status CudaDevice::launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) {
-  SlotState& ss = st_[s.index];
-  GraphInst& gi = ss.gi[s.job.d.type];
+  GraphInst& gi = st_[s.index].gi[s.job.d.type];
   if (!gi.exec) {
     *err = "job type not instantiated";
     return SET_EINVAL;
   }
   const set_status u = update(s, s.job, gi, cost, err);
   if (u != SET_OK) return u;
+  return launch_bound(s, callback, cost, err);
+}
+
+// Bind-at-submit: UpdateGraphParams on the submitting thread (its current device is kept).
+set_status CudaDevice::prepare(Slot& s, LaunchCost* cost, std::string* err) {
+  GraphInst& gi = st_[s.index].gi[s.job.d.type];
+  if (!gi.exec) {
+    *err = "job type not instantiated";
+    return SET_EINVAL;
+  }
+  int old = -1;
+  if (cudaGetDevice(&old) != cudaSuccess) cudaGetLastError();
+  SET_CK(cudaSetDevice(cfg_.device));  // makes the context current for driver calls of the planners
+  const set_status u = update(s, s.job, gi, cost, err);
+  if (old >= 0 && old != cfg_.device) cudaSetDevice(old);
+  return u;
+}
+
+// GraphLaunch of the slot's (already rebound) graph on its lane, and AddCallback.
+set_status CudaDevice::launch_bound(Slot& s, bool callback, LaunchCost* cost, std::string* err) {
+  GraphInst& gi = st_[s.index].gi[s.job.d.type];
   const uint64_t t1 = now_ns();
-  cudaStream_t lane = lanes_[s.lane];
-  SET_CK(cudaGraphLaunch(gi.exec, lane));
+  SET_CK(cudaGraphLaunch(gi.exec, lanes_[s.lane]));
   // cb_mode 2: the graph's own host node runs the completion path
   if (cfg_.cb_mode != 2 && callback) {
     const set_status a = attach_callback(s, err);

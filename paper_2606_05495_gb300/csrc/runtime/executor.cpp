@@ -45,9 +45,10 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   if (!out || cfg.num_streams < 1 || cfg.num_streams > 1024 || cfg.num_workers < 1 || cfg.num_workers > 256 ||
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
       (cfg.io_mode != SET_IO_HOST && cfg.io_mode != SET_IO_DEVICE && cfg.io_mode != SET_IO_MAPPED) ||
-      cfg.cb_mode < 0 || cfg.cb_mode > 3 || (cfg.io_mode == SET_IO_MAPPED && cfg.batch_max > 1)) {
+      cfg.cb_mode < 0 || cfg.cb_mode > 3 || (cfg.io_mode == SET_IO_MAPPED && cfg.batch_max > 1) ||
+      (cfg.bind_at_submit && (cfg.arena_bytes || cfg.batch_max > 1))) {
     *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
-           "cb_mode 0..3, no batched form with SET_IO_MAPPED)";
+           "cb_mode 0..3, no batched form with SET_IO_MAPPED, bind_at_submit without arena or batches)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -74,6 +75,7 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   ex->batch_limit_.store(cfg.batch_max);
   for (uint32_t i = 0; i < L; ++i) ex->queues_.emplace_back(new MpmcRing<JobRec>((size_t)cfg.queue_capacity));
   ex->free_.reset(new MpmcRing<uint32_t>((size_t)L * R));
+  if (cfg.bind_at_submit) ex->ready_.reset(new MpmcRing<uint32_t>((size_t)L * R));
   for (uint32_t i = 0; i < L * R; ++i) ex->free_->push(i);
   for (int w = 0; w < cfg.num_workers; ++w) ex->workers_.emplace_back(&Executor::worker_main, ex.get(), w);
   *out = ex.release();
@@ -171,6 +173,37 @@ set_status Executor::submit(const set_job_desc* d, uint64_t* id_out) {
   if (v != SET_OK) return fail(v, why);
   JobRec j;
   j.d = *d;
+  uint32_t tok = 0;
+  if (ready_ && free_->pop(tok)) {
+    // Algorithm 1 with UpdateGraphParams at submit: bind the job to a free slot now, queue it bound
+    Slot& s = slots_[tok];
+    j.id = c_next_.fetch_add(1);
+    const uint64_t t = now_ns();
+    j.t_submit_ns = d->t_arrival_ns ? d->t_arrival_ns : t;
+    uint64_t z = 0;
+    t_first_ns_.compare_exchange_strong(z, t);
+    j.queued_lane = s.lane;
+    c_submitted_.fetch_add(1);
+    s.job = j;
+    s.batch.clear();
+    s.t_dispatch_ns = 0;
+    s.group_prev = nullptr;
+    LaunchCost cost;
+    std::string e;
+    const set_status st = dev_->prepare(s, &cost, &e);
+    updates_.fetch_add(cost.updates, std::memory_order_relaxed);
+    update_ns_.fetch_add(cost.update_ns, std::memory_order_relaxed);
+    if (st != SET_OK) {
+      fail(st, e);
+      on_complete(s, st);  // the job is accepted and completes with the error
+    } else {
+      ready_->push(tok);  // capacity = all slots: never full
+      free_sig_.notify(1);
+      job_sig_.notify(1);
+    }
+    if (id_out) *id_out = j.id;
+    return SET_OK;
+  }
   bool claimed = false;
   const uint32_t L = (uint32_t)queues_.size();
   for (;;) {
@@ -266,20 +299,29 @@ void Executor::worker_main(int) {
   bool have_carry = false;
   for (;;) {
     uint32_t tok = 0;
+    bool bound = false;
     for (;;) {
       const uint32_t seen = free_sig_.load();
       if (stop_.load()) {
         flush_groups(pending, count);
         return;
       }
+      if (ready_ && ready_->pop(tok)) {  // bound at submit: only the launch is left
+        bound = true;
+        break;
+      }
       if (free_->pop(tok)) break;
       flush_groups(pending, count);  // about to wait: every launched job must own a callback
       if (spin_until([&] { return free_sig_.load() != seen || stop_.load(); }, spin_ns)) continue;
       free_sig_.wait(seen, -1);
     }
+    if (bound) {
+      launch_slot(slots_[tok], true, pending, count, every);
+      continue;
+    }
     Slot& s = slots_[tok];
     JobRec j;
-    bool stolen = false, got = false;
+    bool stolen = false, got = false, yielded = false;
     for (;;) {
       const uint32_t seen = job_sig_.load();
       if (have_carry) {
@@ -290,6 +332,12 @@ void Executor::worker_main(int) {
       }
       if (find_job(s.lane, j, stolen)) {
         got = true;
+        break;
+      }
+      if (ready_ && ready_->size_approx() > 0) {  // a bound job waits for a launcher: give the slot back
+        free_->push(tok);
+        free_sig_.notify(1);
+        yielded = true;
         break;
       }
       flush_groups(pending, count);
@@ -306,6 +354,7 @@ void Executor::worker_main(int) {
       job_sig_.wait(seen, -1);
     }
     if (!got) {
+      if (yielded) continue;
       if (stop_.load() && cfg_.steal) {
         free_->push(tok);
         return;
@@ -353,31 +402,40 @@ void Executor::worker_main(int) {
         continue;
       }
     }
-    if (sticky_.load() != SET_OK) {
-      on_complete(s, sticky_.load());
-      continue;
-    }
-    s.t_dispatch_ns = now_ns();  // admitted: from here on the job is being launched
-    LaunchCost cost;
-    std::string e;
-    s.group_prev = pending[s.lane];
-    const bool close = ++count[s.lane] >= every;
-    const set_status st = s.batch.empty() ? dev_->launch(s, close, &cost, &e) : dev_->launch_batch(s, close, &cost, &e);
-    if (st == SET_OK) {
-      pending[s.lane] = close ? nullptr : &s;
-      if (close) count[s.lane] = 0;
-    } else {
-      count[s.lane] -= 1;
-    }
-    updates_.fetch_add(cost.updates, std::memory_order_relaxed);
-    update_ns_.fetch_add(cost.update_ns, std::memory_order_relaxed);
-    launch_ns_.fetch_add(cost.launch_ns, std::memory_order_relaxed);
-    launched_.fetch_add(1, std::memory_order_relaxed);
-    if (st != SET_OK) {
-      fail(st, e);
-      s.group_prev = nullptr;
-      on_complete(s, st);
-    }
+    launch_slot(s, false, pending, count, every);
+  }
+}
+
+// LaunchJob + AddCallback for a slot that holds its job (bound: its graph was already rebound at
+// submit).  The slot joins its lane's open completion group, which closes every `every` launches.
+void Executor::launch_slot(Slot& s, bool bound, std::vector<Slot*>& pending, std::vector<int>& count, int every) {
+  if (sticky_.load() != SET_OK) {
+    s.group_prev = nullptr;
+    on_complete(s, sticky_.load());
+    return;
+  }
+  s.t_dispatch_ns = now_ns();  // admitted: from here on the job is being launched
+  LaunchCost cost;
+  std::string e;
+  s.group_prev = pending[s.lane];
+  const bool close = ++count[s.lane] >= every;
+  const set_status st = bound            ? dev_->launch_bound(s, close, &cost, &e)
+                        : s.batch.empty() ? dev_->launch(s, close, &cost, &e)
+                                          : dev_->launch_batch(s, close, &cost, &e);
+  if (st == SET_OK) {
+    pending[s.lane] = close ? nullptr : &s;
+    if (close) count[s.lane] = 0;
+  } else {
+    count[s.lane] -= 1;
+  }
+  updates_.fetch_add(cost.updates, std::memory_order_relaxed);
+  update_ns_.fetch_add(cost.update_ns, std::memory_order_relaxed);
+  launch_ns_.fetch_add(cost.launch_ns, std::memory_order_relaxed);
+  launched_.fetch_add(1, std::memory_order_relaxed);
+  if (st != SET_OK) {
+    fail(st, e);
+    s.group_prev = nullptr;
+    on_complete(s, st);
   }
 }
 

@@ -60,6 +60,10 @@ class Device {
   // `callback` is set: the callback, run after the D2H copy, must call
   // Executor::on_complete_group(slot) (the slot and every slot chained through group_prev).
   virtual set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) = 0;
+  // UpdateGraphParams alone (bind-at-submit): the slot's graph is rebound to s.job now and a later
+  // launch_bound(s) launches it without updating.
+  virtual set_status prepare(Slot& s, LaunchCost* cost, std::string* err) = 0;
+  virtual set_status launch_bound(Slot& s, bool callback, LaunchCost* cost, std::string* err) = 0;
   // Batched form: one launch of the slot's batch graph over the jobs in s.batch (same type).
   virtual set_status launch_batch(Slot& s, bool callback, LaunchCost* cost, std::string* err) = 0;
   // AddCallback alone: completes the group ending at `s` (already launched) on its lane.
@@ -118,6 +122,7 @@ class Executor {
   explicit Executor(const set_config& cfg);
   void worker_main(int w);
   void flush_groups(std::vector<Slot*>& pending, std::vector<int>& count);
+  void launch_slot(Slot& s, bool bound, std::vector<Slot*>& pending, std::vector<int>& count, int every);
   bool find_job(uint32_t lane, JobRec& j, bool& stolen);  // Alg. 2 FindJob
   set_status validate(const set_job_desc& d, std::string* why) const;
   set_status fail(set_status st, const std::string& msg);
@@ -131,6 +136,7 @@ class Executor {
   std::vector<Slot> slots_;
   std::vector<std::unique_ptr<MpmcRing<JobRec>>> queues_;  // Q_i, one per lane
   std::unique_ptr<MpmcRing<uint32_t>> free_;                // W_pool of slot indices
+  std::unique_ptr<MpmcRing<uint32_t>> ready_;               // bind-at-submit: slots bound to a job
   std::vector<std::thread> workers_;
 
   Signal free_sig_, job_sig_, space_sig_, done_sig_;

@@ -75,6 +75,22 @@ class SimDevice final : public Device {
     return launch(s, callback, cost, err);
   }
 
+  set_status prepare(Slot&, LaunchCost* cost, std::string*) override {
+    cost->updates += 3;
+    return SET_OK;
+  }
+
+  set_status launch_bound(Slot& s, bool callback, LaunchCost*, std::string* err) override {
+    const uint64_t k = ++launches_;
+    if (fail_ && k % fail_ == 0) {
+      *err = "simulated launch failure";
+      return SET_ECUDA;
+    }
+    enqueue(&s, k, false);
+    if (callback) enqueue(&s, 0, true);
+    return SET_OK;
+  }
+
   set_status autotune(uint32_t, const JobRec*, size_t, int, set_tune_result*, std::string* err) override {
     *err = "the autotuner needs the CUDA device";
     return SET_EINVAL;

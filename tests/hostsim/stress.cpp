@@ -20,6 +20,7 @@ int main(int argc, char** argv) {
   cfg.queue_capacity = 2;
   cfg.slot_bytes = 1 << 20;
   cfg.cb_every = argc > 2 ? std::atoi(argv[2]) : 1;
+  cfg.bind_at_submit = argc > 3 ? std::atoi(argv[3]) : 0;
   set_ctx* ctx = nullptr;
   if (set_create_ex(&cfg, &ctx) != SET_OK) {
     std::fprintf(stderr, "create failed: %s\n", set_last_error(nullptr));

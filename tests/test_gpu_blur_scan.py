@@ -158,3 +158,15 @@ def test_smallest_job_in_a_slot_sized_for_it(kind):
     assert st["completed"] == 1 and st["failed"] == 0
     {"blur": check_blur, "scan": check_scan, "img": check_img}[kind](job)
     check_trailers([job])
+
+
+@pytest.mark.parametrize("cb_mode,workers", [(0, 1), (3, 2)])
+def test_bind_at_submit(cb_mode, workers):
+    # UpdateGraphParams on the submitting thread, dispatch only launches
+    jobs = [scan_job(800 + k, n=40000 + 13 * k) for k in range(60)] + [blur_job(900 + k) for k in range(40)]
+    st = run_jobs(jobs, num_streams=4, num_workers=workers, ring_depth=2, slot_bytes=1 << 20, cb_mode=cb_mode,
+                  bind_at_submit=1)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+    check_trailers(jobs)

@@ -257,8 +257,39 @@ def test_sanitizer_stress(san):
     exe = hostsim_util.build_stress(san)
     env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1 exitcode=66", ASAN_OPTIONS="detect_leaks=1 exitcode=66",
                SET_SIM_DELAY_US="0,20")
-    for k in ("SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY"):
+    for k in ("SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY", "SET_SIM_SLOW_LANE"):
         env.pop(k, None)
-    for every in ("1", "3"):
-        r = subprocess.run([exe, "6000", every], capture_output=True, text=True, env=env, timeout=600)
-        assert r.returncode == 0, r.stdout + r.stderr[-3000:]
+    for every, bind in (("1", "0"), ("3", "0"), ("1", "1"), ("3", "1")):
+        r = subprocess.run([exe, "6000", every, bind], capture_output=True, text=True, env=env, timeout=600)
+        assert r.returncode == 0, (every, bind, r.stdout + r.stderr[-3000:])
+
+
+@pytest.mark.parametrize("workers,every", [(1, 1), (3, 1), (2, 4)])
+def test_bind_at_submit_every_job_once(sim, workers, every):
+    # UpdateGraphParams at submit: the submitter binds a free slot, dispatch only launches; jobs
+    # that find no free slot are bound at dispatch as usual
+    os.environ["SET_SIM_DELAY_US"] = "1,30"
+    n = 2000
+    jobs = Jobs(n)
+    ctx = create(sim, num_streams=4, num_workers=workers, ring_depth=2, queue_capacity=4, cb_every=every,
+                 bind_at_submit=1)
+    rc, first, done = submit_all(sim, ctx, jobs, n)
+    assert rc == 0 and done == n
+    assert sim.set_wait_all(ctx, 30_000_000) == 0
+    st = stats(sim, ctx)
+    sim.set_destroy(ctx)
+    assert st.submitted == st.completed == n and st.failed == 0 and st.canary_errors == 0, st.as_dict()
+    assert np.array_equal(np.sort(jobs.trailer_ids()), np.arange(first, first + n, dtype=np.uint64))
+    assert all(s == 0 for s in jobs.status)
+
+
+def test_bind_at_submit_refused_with_arena_or_batches(sim):
+    for kw in (dict(arena_bytes=1 << 24), dict(batch_max=4)):
+        cfg = B.set_config()
+        sim.set_config_default(ctypes.byref(cfg))
+        cfg.slot_bytes = 1 << 16
+        cfg.bind_at_submit = 1
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        ctx = ctypes.c_void_p()
+        assert sim.set_create_ex(ctypes.byref(cfg), ctypes.byref(ctx)) == B.SET_EINVAL
