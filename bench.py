@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot"], default="scan",
+    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study"], default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
     p.add_argument("--clock-ms", type=float, default=25.0, help="clock sampling period in timed regions")
     p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
@@ -686,6 +686,32 @@ def _kernel_only(S, js, n, launches):
     print(json.dumps({"kernel_only": js.kind, "jobs": launches}), flush=True)
 
 
+def run_bind_study(args, d: Dist):
+    """UpdateGraphParams at dispatch vs at submit (set_config.bind_at_submit) on the scan jobs: one
+    JSON line per (io mode, completion mode, dispatch threads, bind)."""
+    import paper_2606_05495_gb300 as S
+    t = _torch()
+    t.cuda.set_device(d.local)
+    w = Workload(S, shard(args.jobs, d.rank), d.local)
+    nj = len(w.ids)
+    for io in (S.SET_IO_HOST, S.SET_IO_DEVICE):
+        descs = w.descs_host if io == S.SET_IO_HOST else w.descs_dev
+        for cbm, every, workers in ((0, 8, 1), (0, 1, 1), (3, 1, 1), (3, 1, 2), (3, 1, 4)):
+            for bind in (0, 1):
+                cfg = dict(num_streams=args.streams, num_workers=workers, ring_depth=args.ring, cb_mode=cbm,
+                           cb_every=every, device=d.local, io_mode=io, bind_at_submit=bind,
+                           slot_bytes=S.set_job_slot_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)))
+                ctx = S.create(S.default_config(**cfg))
+                ms, st = timed(S, ctx, descs, nj, args, d)
+                S.set_destroy(ctx)
+                if d.rank == 0:
+                    print(json.dumps({"workload": "bind-study", "io": "host" if io == S.SET_IO_HOST else "device",
+                                      "cb_mode": cbm, "cb_every": every, "workers": workers, "bind_at_submit": bind,
+                                      "jobs_per_s": nj * d.world / (ms * 1e-3), "p99_us": st["p99_us"],
+                                      "mean_update_us": st["mean_update_us"], "mean_launch_us": st["mean_launch_us"],
+                                      "mean_queue_us": st["mean_queue_us"]}), flush=True)
+
+
 def run_workload(args, d: Dist):
     """One JSON line per workload: SET forms against the batch-synchronous graph baseline."""
     import paper_2606_05495_gb300 as S
@@ -851,6 +877,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, d)
+        elif args.workload == "bind-study":
+            run_bind_study(args, d)
         elif args.workload != "scan":
             run_workload(args, d)
         else:
