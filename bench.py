@@ -852,9 +852,12 @@ def run_workload(args, d: Dist):
             row = {"rate": lam}
             # set: completion by the polling thread (cb_mode 3); set_host_callbacks: Algorithm 3's
             # host function on the lane stream (cb_mode 1)
-            for name, mode, cbm in (("set", S.SET_SERVE_SET, 3), ("set_host_callbacks", S.SET_SERVE_SET, 1),
-                                    ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1)):
-                ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm)))
+            # set_launch_at_submit: the request loop binds and launches an arrival itself when a slot
+            # and its memory are free (bind_at_submit 2), no hand-off to a dispatch thread
+            for name, mode, cbm, bind in (("set", S.SET_SERVE_SET, 3, 0), ("set_launch_at_submit", S.SET_SERVE_SET, 3, 2),
+                                          ("set_host_callbacks", S.SET_SERVE_SET, 1, 0),
+                                          ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1, 0)):
+                ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm, bind_at_submit=bind)))
                 st = S.set_stats_t()
                 with clocks.window():
                     S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)

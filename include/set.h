@@ -175,8 +175,11 @@ typedef struct {
                           to the slot it pops); 1: at submit, as Algorithm 1 lists it: the
                           submitting thread takes a free slot if one is ready, rebinds the slot's
                           graph to the job and queues it bound, so dispatch threads only launch
-                          (jobs that find no free slot are bound at dispatch).  Not with
-                          arena_bytes or batch_max > 1. */
+                          (jobs that find no free slot are bound at dispatch); 2: as 1, and the
+                          submitting thread also launches the bound job (one completion per job),
+                          so an idle executor starts a job without waking a dispatch thread.  With
+                          arena_bytes the job is bound at submit only if its block is free then.
+                          Not with batch_max > 1. */
 } set_config;
 
 typedef struct {

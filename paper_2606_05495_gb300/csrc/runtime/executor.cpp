@@ -46,9 +46,9 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
       (cfg.io_mode != SET_IO_HOST && cfg.io_mode != SET_IO_DEVICE && cfg.io_mode != SET_IO_MAPPED) ||
       cfg.cb_mode < 0 || cfg.cb_mode > 3 || (cfg.io_mode == SET_IO_MAPPED && cfg.batch_max > 1) ||
-      (cfg.bind_at_submit && (cfg.arena_bytes || cfg.batch_max > 1))) {
+      cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1)) {
     *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
-           "cb_mode 0..3, no batched form with SET_IO_MAPPED, bind_at_submit without arena or batches)";
+           "cb_mode 0..3, no batched form with SET_IO_MAPPED or bind_at_submit)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -174,7 +174,18 @@ set_status Executor::submit(const set_job_desc* d, uint64_t* id_out) {
   JobRec j;
   j.d = *d;
   uint32_t tok = 0;
-  if (ready_ && free_->pop(tok)) {
+  bool have_slot = ready_ && free_->pop(tok);
+  if (have_slot && use_arena_) {
+    // arena mode: the job also needs its device block now; without one it is bound at dispatch
+    Slot& s = slots_[tok];
+    s.job_mem = arena_.alloc(job_block_bytes(*d), &s.job_mem_bytes);
+    if (!s.job_mem) {
+      free_->push(tok);
+      free_sig_.notify(1);
+      have_slot = false;
+    }
+  }
+  if (have_slot) {
     // Algorithm 1 with UpdateGraphParams at submit: bind the job to a free slot now, queue it bound
     Slot& s = slots_[tok];
     j.id = c_next_.fetch_add(1);
@@ -196,6 +207,21 @@ set_status Executor::submit(const set_job_desc* d, uint64_t* id_out) {
     if (st != SET_OK) {
       fail(st, e);
       on_complete(s, st);  // the job is accepted and completes with the error
+    } else if (cfg_.bind_at_submit == 2) {
+      // launch at submit: the submitting thread is the dispatcher (one callback per job)
+      if (sticky_.load() != SET_OK) {
+        on_complete(s, sticky_.load());
+      } else {
+        s.t_dispatch_ns = now_ns();
+        LaunchCost lc;
+        const set_status ls = dev_->launch_bound(s, true, &lc, &e);
+        launch_ns_.fetch_add(lc.launch_ns, std::memory_order_relaxed);
+        launched_.fetch_add(1, std::memory_order_relaxed);
+        if (ls != SET_OK) {
+          fail(ls, e);
+          on_complete(s, ls);
+        }
+      }
     } else {
       ready_->push(tok);  // capacity = all slots: never full
       free_sig_.notify(1);

@@ -63,6 +63,15 @@ def test_serving_polled_completion():
         check_any(j)
 
 
+def test_serving_launch_at_submit():
+    # the request loop binds and launches each arrival itself when a slot and its memory are free
+    jobs, arrivals = serve_jobs(8000.0, 120, img_cap=1024)
+    st = _serve(jobs, arrivals, S().SET_SERVE_SET, cb_mode=3, bind_at_submit=2, **ARENA_CFG)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        check_any(j)
+
+
 def test_serving_batch_sync_baseline_same_arrivals():
     jobs, arrivals = serve_jobs(4000.0, 80, img_cap=1024)
     st = _serve(jobs, arrivals, S().SET_SERVE_BATCH_SYNC, **ARENA_CFG)

@@ -259,20 +259,21 @@ def test_sanitizer_stress(san):
                SET_SIM_DELAY_US="0,20")
     for k in ("SET_SIM_DROP_EVERY", "SET_SIM_BADGEN_EVERY", "SET_SIM_FAIL_EVERY", "SET_SIM_SLOW_LANE"):
         env.pop(k, None)
-    for every, bind in (("1", "0"), ("3", "0"), ("1", "1"), ("3", "1")):
+    for every, bind in (("1", "0"), ("3", "0"), ("1", "1"), ("3", "1"), ("1", "2")):
         r = subprocess.run([exe, "6000", every, bind], capture_output=True, text=True, env=env, timeout=600)
         assert r.returncode == 0, (every, bind, r.stdout + r.stderr[-3000:])
 
 
-@pytest.mark.parametrize("workers,every", [(1, 1), (3, 1), (2, 4)])
-def test_bind_at_submit_every_job_once(sim, workers, every):
+@pytest.mark.parametrize("workers,every,bind,arena", [(1, 1, 1, 0), (3, 1, 1, 0), (2, 4, 1, 0), (2, 1, 2, 0),
+                                                     (1, 1, 2, 1 << 22), (2, 2, 1, 1 << 22)])
+def test_bind_at_submit_every_job_once(sim, workers, every, bind, arena):
     # UpdateGraphParams at submit: the submitter binds a free slot, dispatch only launches; jobs
     # that find no free slot are bound at dispatch as usual
     os.environ["SET_SIM_DELAY_US"] = "1,30"
     n = 2000
     jobs = Jobs(n)
     ctx = create(sim, num_streams=4, num_workers=workers, ring_depth=2, queue_capacity=4, cb_every=every,
-                 bind_at_submit=1)
+                 bind_at_submit=bind, arena_bytes=arena)
     rc, first, done = submit_all(sim, ctx, jobs, n)
     assert rc == 0 and done == n
     assert sim.set_wait_all(ctx, 30_000_000) == 0
@@ -283,8 +284,8 @@ def test_bind_at_submit_every_job_once(sim, workers, every):
     assert all(s == 0 for s in jobs.status)
 
 
-def test_bind_at_submit_refused_with_arena_or_batches(sim):
-    for kw in (dict(arena_bytes=1 << 24), dict(batch_max=4)):
+def test_bind_at_submit_refused_with_batches(sim):
+    for kw in (dict(batch_max=4), dict(bind_at_submit=3)):
         cfg = B.set_config()
         sim.set_config_default(ctypes.byref(cfg))
         cfg.slot_bytes = 1 << 16
