@@ -673,6 +673,53 @@ def _copy_bound(S, js, n, streams, e2e_jobs_per_s):
             "e2e_frac_of_bound": e2e_jobs_per_s * t / n}
 
 
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def _job_kernel_times(S, js, n, jobs=256):
+    """Mean device time (us) of each job's kernel chain launched alone (set_launch_job) on one
+    stream, with CUDA events on that stream around every job; a sleep kernel holds the stream
+    while the launches are enqueued so the events bracket device time only.  Resident inputs."""
+    t = _torch()
+    st = t.cuda.Stream()
+    sb = max(S.set_job_scratch_bytes(js.kind, S.dims4(*dd)) for dd in js.dims)
+    scratch = t.zeros(max(sb, 256), dtype=t.uint8, device="cuda")
+    m = min(n, jobs)
+    evs = [(t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)) for _ in range(m)]
+    with t.cuda.stream(st):
+        for k in range(min(m, 8)):  # warm-up
+            dd = js.descs_dev[k]
+            S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st.cuda_stream),
+                    "set_launch_job")
+        st.synchronize()
+        t.cuda._sleep(int(2e9 * 40e-6 * m))
+        for k in range(m):
+            dd = js.descs_dev[k]
+            evs[k][0].record(st)
+            S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st.cuda_stream)
+            evs[k][1].record(st)
+    st.synchronize()
+    return [a.elapsed_time(b) * 1e3 for a, b in evs], m
+
+
+def _roofline_hbm(kernel, alg_bytes_per_job, job_us, launches_per_job=1):
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    ach = alg_bytes_per_job / (job_us * 1e-6) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "alg_bytes_per_job": alg_bytes_per_job, "job_us": job_us, "launches_per_job": launches_per_job,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def _eq4(line, bound_jobs_per_s):
+    """Eq. 4 schedule fraction 1 - T_ideal / T_measured of every arm of a workload line."""
+    return {k: 1 - v["jobs_per_s"] / bound_jobs_per_s for k, v in line.items()
+            if isinstance(v, dict) and v.get("jobs_per_s")}
+
+
 def _kernel_only(S, js, n, launches):
     """Profiling: the stage kernels of `launches` resident jobs alone on one stream, then exit."""
     t = _torch()
@@ -739,7 +786,10 @@ def run_workload(args, d: Dist):
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
         line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"])
+        line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
+        ts, m = _job_kernel_times(S, js, n)
+        line["roofline"] = _roofline_hbm("blur_hist_kernel", 2 * 65536 + 1040, statistics.mean(ts))
         # kernels reading and writing the pinned buffers over NVLink-C2C, no copy nodes
         line["set_mapped_io"] = _rate(S, dict(polled, io_mode=S.SET_IO_MAPPED), js.descs, n, args, d)
     elif args.workload in ("img", "mlp"):
@@ -770,7 +820,23 @@ def run_workload(args, d: Dist):
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         best = max(line["set_per_job"]["jobs_per_s"], line["set_batched"]["jobs_per_s"])
         line["pipeline"] = _copy_bound(S, js, n, 16, best)
+        line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
+        dev = JobSet(S, kind, range(min(n, 256)), device_copy=True)  # resident copies for the kernels alone
+        ts, m = _job_kernel_times(S, dev, len(dev.ids))
+        if kind == 3:
+            px = [W * H for (W, H) in dev.dims[:m]]
+            alg = statistics.mean(4 * p + 1040 for p in px)  # read RGB, write Sobel + histogram
+            line["roofline"] = _roofline_hbm("img_fused_kernel", alg, statistics.mean(ts))
+        else:
+            rows = [dd[0] for dd in dev.dims[:m]]
+            flop = statistics.mean(2 * 2 * r * 1024 * 4096 for r in rows)
+            pk = _peaks().get("bf16_tflops", 1900.0)
+            ach = flop / (statistics.mean(ts) * 1e-6) / 1e12
+            line["roofline"] = {"bound": "tensor", "kernel": "mlp_gemm_kernel (+ layernorm_kernel)", "achieved": ach,
+                                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "flop_per_job": flop,
+                                "job_us": statistics.mean(ts), "launches_per_job": 3,
+                                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)"}
         if kind == 4:
             flop = 2.0 * js.rows() * 1024 * 4096 * 2
             line["gemm_tflops_e2e"] = {k: flop / (line[k]["ms_per_step"] * 1e-3) / 1e12
@@ -792,6 +858,7 @@ def run_workload(args, d: Dist):
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
         line["pipeline"] = _copy_bound(S, js, n, 16, line["set_polled_2_workers"]["jobs_per_s"])
+        line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, dict(cfg, cb_mode=3, num_workers=2), js.descs, n)
         # the kernel chain alone: CUDA events around each job's 8 launches on one stream
         st = t.cuda.Stream()

@@ -232,7 +232,11 @@ void CudaDevice::poll_main() {
       continue;
     }
     if (poll_stop_.load()) return;
-    poll_sig_.wait(seen, 100 * 1000000ll);
+    // idle: spin spin_us on the signal first (a job launched meanwhile needs no futex wake), then sleep
+    const uint64_t t_end = now_ns() + (uint64_t)(cfg_.spin_us > 0 ? cfg_.spin_us : 0) * 1000ull;
+    while (poll_sig_.load() == seen && !poll_stop_.load() && now_ns() < t_end) {
+    }
+    if (poll_sig_.load() == seen) poll_sig_.wait(seen, 100 * 1000000ll);
   }
 }
 
