@@ -808,7 +808,8 @@ def run_workload(args, d: Dist):
         if kind == 3:
             line["set_per_stage_graphs"] = _rate(S, dict(polled, img_fused=0), js.descs, n, args, d)
         # batched form: autotuned jobs per launch (and tile / CTAs per SM for images) in an 8 GiB arena
-        bcfg = dict(cfg, cb_every=2, ring_depth=2, batch_max=16, arena_bytes=8 << 30, slot_bytes=1 << 30)
+        # polled completion: a batch launch's host-callback chain would cost more than its copies
+        bcfg = dict(cfg, cb_mode=3, ring_depth=2, batch_max=16, arena_bytes=8 << 30, slot_bytes=1 << 30)
         ctx = S.create(S.default_config(**bcfg))
         tune = S.set_tune_result()
         ns = min(n, 64)
