@@ -93,6 +93,11 @@ typedef enum {
 
 /* set_job_desc.flags */
 #define SET_F_NONBLOCK 0x1u /* set_submit returns SET_EAGAIN instead of waiting for queue room */
+#define SET_F_TEST_STALL 0x100u /* test hook for failure detection without a GPU fault: in a scan
+                                   job of >= 3 tiles, tile 1 exits without publishing, so tile 2's
+                                   look-back and the final max gather wait until their bounded
+                                   limit (~0.1-0.4 s) runs out; the job completes with SET_EDEVICE
+                                   (trailer error bit SET_DEVERR_WAIT) and the context stays usable */
 
 /* The last 16 bytes of every job's output. */
 typedef struct {

@@ -57,6 +57,7 @@ struct ScanArgs {
   uint32_t n, T;
   float a;
   uint32_t slot_gen;
+  uint32_t skip_tile;  // test hook (SET_F_TEST_STALL): this tile never publishes; else ~0u
 };
 
 __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
@@ -87,6 +88,10 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   // latency overlaps the data loads.
   stamp_entry(p.stamp);
   const uint32_t tile = blockIdx.x;
+  if (tile == p.skip_tile) {  // test hook: the look-back of the next tile and the max gather time out
+    stamp_exit(p.stamp);
+    return;
+  }
   const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&hdr->epoch) & 0x3FFFFFFFu;
   const uint32_t n = p.n;
   const size_t base = (size_t)tile * kTile + (size_t)tid * kPer;
@@ -289,6 +294,7 @@ bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* 
   a.T = num_tiles(n);
   a.a = in.scalar;
   a.slot_gen = in.slot_gen;
+  a.skip_tile = (in.flags & SET_F_TEST_STALL) && a.T >= 3 ? 1u : ~0u;
   KernelLaunch& k = kl[0];
   k.func = reinterpret_cast<const void*>(&saxpy_scan_max_kernel);
   k.grid = dim3(a.T);

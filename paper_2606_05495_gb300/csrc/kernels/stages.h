@@ -61,6 +61,7 @@ struct KernelLaunch {
 
 struct JobPlanIn {
   uint32_t type = 0;
+  uint32_t flags = 0;  // set_job_desc.flags
   uint32_t dims[4] = {0, 0, 0, 0};
   float scalar = 0.f;
   const void* shared[2] = {nullptr, nullptr};

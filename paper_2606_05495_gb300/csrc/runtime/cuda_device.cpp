@@ -334,6 +334,7 @@ bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::
   setk::place_job(L, s.job_mem ? 0 : ctl_);
   setk::JobPlanIn in;
   in.type = j.d.type;
+  in.flags = j.d.flags;
   std::memcpy(in.dims, j.d.dims, sizeof in.dims);
   in.scalar = j.d.scalar;
   in.shared[0] = j.d.shared[0];

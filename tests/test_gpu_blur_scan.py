@@ -170,3 +170,21 @@ def test_bind_at_submit(cb_mode, workers):
     for j in jobs:
         (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
     check_trailers(jobs)
+
+
+def test_bounded_device_wait_reports_and_context_survives():
+    # failure detection without a GPU fault: a scan tile that never publishes makes the next tile's
+    # look-back (and the final max gather) wait until its bound runs out; the job completes with
+    # SET_EDEVICE (trailer error bit), its neighbours on the same slot are unaffected
+    s = S()
+    jobs = [scan_job(1000 + k, n=65536) for k in range(5)]
+    jobs[2].desc.flags = s.SET_F_TEST_STALL
+    slot = s.set_job_slot_bytes(s.SET_JOB_SAXPY_SCAN_MAX, s.dims4(65536))
+    st = run_jobs(jobs, num_streams=1, num_workers=1, ring_depth=1, slot_bytes=slot, cb_mode=3)
+    assert st["completed"] == 5 and st["failed"] == 1 and st["canary_errors"] == 0, st
+    assert jobs[2].status.value == s.SET_EDEVICE
+    _, _, word = jobs[2].trailer()
+    assert word == (s.SET_TRAILER_MAGIC << 16) | s.SET_DEVERR_WAIT, hex(word)
+    for k in (0, 1, 3, 4):
+        assert jobs[k].status.value == s.SET_OK
+        check_scan(jobs[k])
