@@ -134,8 +134,11 @@ typedef struct {
  *                  directly over the host link, so a job's graph has no copy nodes.  An addition
  *                  for hosts coherently attached to the GPU (NVLink-C2C); not for MLP jobs,
  *                  whose x feeds TMA loads (SET_EINVAL), nor for the batched form or baselines.
- *                  Buffers the device cannot address are rejected at submit with SET_EINVAL. */
-typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1, SET_IO_MAPPED = 2 } set_io_mode;
+ *                  Buffers the device cannot address are rejected at submit with SET_EINVAL.
+ *   SET_IO_MAPPED_IN   in as SET_IO_MAPPED (no H2D node), out by the D2H copy node.
+ *   SET_IO_MAPPED_OUT  in by the H2D copy node, out as SET_IO_MAPPED (the kernels store the job's
+ *                  results straight into the pinned host buffer; no D2H node).  MLP jobs allowed. */
+typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1, SET_IO_MAPPED = 2, SET_IO_MAPPED_IN = 3, SET_IO_MAPPED_OUT = 4 } set_io_mode;
 
 typedef struct {
   int num_streams;     /* lanes b (paper's workers), >= 1 */

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "SET_OK", -1: "SET_EINVAL", -2: "SET_ENOMEM", -3: "SET_EAGAIN
 SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX, SET_JOB_IMG_SOBEL_HIST, SET_JOB_MLP_LN, SET_JOB_HOTSPOT = 1, 2, 3, 4, 5
 SET_F_NONBLOCK = 0x1
 SET_F_TEST_STALL = 0x100
-SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED = 0, 1, 2
+SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED, SET_IO_MAPPED_IN, SET_IO_MAPPED_OUT = 0, 1, 2, 3, 4
 SET_BASE_SYNC, SET_BASE_BATCH_SYNC = 1, 2
 SET_SERVE_SET, SET_SERVE_BATCH_SYNC = 0, 1
 SET_TRAILER_MAGIC = 0x5E7C

@@ -339,13 +339,9 @@ bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::
   in.scalar = j.d.scalar;
   in.shared[0] = j.d.shared[0];
   in.shared[1] = j.d.shared[1];
-  if (cfg_.io_mode == SET_IO_MAPPED) {  // kernels address the job's host buffers directly
-    in.d_in = j.d.in ? j.d.in : ph_dev_;
-    in.d_out = j.d.out ? j.d.out : ph_dev_;
-  } else {
-    in.d_in = base + L->in_off;
-    in.d_out = base + L->out_off;
-  }
+  // mapped sides: the kernels address the job's host buffer directly
+  in.d_in = io_maps_in(cfg_.io_mode) ? (j.d.in ? j.d.in : ph_dev_) : base + L->in_off;
+  in.d_out = io_maps_out(cfg_.io_mode) ? (j.d.out ? j.d.out : ph_dev_) : base + L->out_off;
   in.d_scratch = base + L->scratch_off;
   in.d_persist = s.dev + setk::control_offset(j.d.type);
   in.job_id = j.id;
@@ -371,17 +367,17 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   uint8_t* base = s.job_mem ? s.job_mem : s.dev;
   GraphInst& gi = st_[s.index].gi[type];
   SET_CK(cudaGraphCreate(&gi.graph, 0));
-  const bool copies = cfg_.io_mode != SET_IO_MAPPED;  // mapped: the kernels read and write host memory
-  const void* src_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
-  void* dst_ph = cfg_.io_mode == SET_IO_HOST ? ph_host_ : ph_dev_;
-  if (copies)
+  const bool copy_in = !io_maps_in(cfg_.io_mode), copy_out = !io_maps_out(cfg_.io_mode);
+  const void* src_ph = cfg_.io_mode == SET_IO_DEVICE ? ph_dev_ : ph_host_;
+  void* dst_ph = cfg_.io_mode == SET_IO_DEVICE ? ph_dev_ : ph_host_;
+  if (copy_in)
     SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, nullptr, 0, base + L.in_off, src_ph, L.in_bytes, kind_in_));
   uint32_t has_dependents = 0;
   for (int k = 0; k < nk; ++k) {
     cudaGraphNode_t deps[setk::kMaxKernels];
     size_t nd = 0;
     if (kl[k].deps == 0) {
-      if (copies) deps[nd++] = gi.h2d;
+      if (copy_in) deps[nd++] = gi.h2d;
     } else {
       for (int q = 0; q < k; ++q)
         if (kl[k].deps & (1u << q)) {
@@ -396,14 +392,14 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   size_t ns = 0;
   for (int k = 0; k < nk; ++k)
     if (!(has_dependents & (1u << k))) sinks[ns++] = gi.kn[k];
-  if (copies)
+  if (copy_out)
     SET_CK(cudaGraphAddMemcpyNode1D(&gi.d2h, gi.graph, sinks, ns, dst_ph, base + L.out_off, L.out_bytes, kind_out_));
   if (cfg_.cb_mode == 2) {  // Algorithm 3's callback as the graph's last node, bound to this slot
     cudaHostNodeParams hp{};
     hp.fn = host_complete;
     hp.userData = &s;
     cudaGraphNode_t hn;
-    if (copies)
+    if (copy_out)
       SET_CK(cudaGraphAddHostNode(&hn, gi.graph, &gi.d2h, 1, &hp));
     else
       SET_CK(cudaGraphAddHostNode(&hn, gi.graph, sinks, ns, &hp));
@@ -428,18 +424,18 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
   uint8_t* base = s.job_mem ? s.job_mem : s.dev;
   const uint64_t t0 = now_ns();
   arm_stamps(const_cast<Slot&>(s), kl, nk);
-  const bool copies = cfg_.io_mode != SET_IO_MAPPED;
+  const bool copy_in = !io_maps_in(cfg_.io_mode), copy_out = !io_maps_out(cfg_.io_mode);
   cudaError_t e = cudaSuccess;
-  if (copies) e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
+  if (copy_in) e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
   if (e == cudaSuccess)
     for (int k = 0; k < nk && e == cudaSuccess; ++k) {
       const cudaKernelNodeParams p = node_params(kl[k]);
       e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.kn[k], &p);
     }
-  if (e == cudaSuccess && copies)
+  if (e == cudaSuccess && copy_out)
     e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.d2h, j.d.out, base + L.out_off, L.out_bytes, kind_out_);
   cost->update_ns += now_ns() - t0;
-  cost->updates += (uint64_t)nk + (copies ? 2 : 0);
+  cost->updates += (uint64_t)nk + (copy_in ? 1 : 0) + (copy_out ? 1 : 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *err = std::string("graph parameter update rejected (host buffers must be pinned, device buffers must be on "

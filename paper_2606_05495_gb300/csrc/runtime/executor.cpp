@@ -44,11 +44,11 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   normalize(cfg);
   if (!out || cfg.num_streams < 1 || cfg.num_streams > 1024 || cfg.num_workers < 1 || cfg.num_workers > 256 ||
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
-      (cfg.io_mode != SET_IO_HOST && cfg.io_mode != SET_IO_DEVICE && cfg.io_mode != SET_IO_MAPPED) ||
-      cfg.cb_mode < 0 || cfg.cb_mode > 3 || (cfg.io_mode == SET_IO_MAPPED && cfg.batch_max > 1) ||
+      cfg.io_mode < SET_IO_HOST || cfg.io_mode > SET_IO_MAPPED_OUT || cfg.cb_mode < 0 || cfg.cb_mode > 3 ||
+      ((io_maps_in(cfg.io_mode) || io_maps_out(cfg.io_mode)) && cfg.batch_max > 1) ||
       cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1)) {
     *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
-           "cb_mode 0..3, no batched form with SET_IO_MAPPED or bind_at_submit)";
+           "cb_mode 0..3, no batched form with mapped I/O or bind_at_submit)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -129,15 +129,14 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
     *why = "MLP job needs device weights in shared[0], shared[1]";
     return SET_EINVAL;
   }
-  if (cfg_.io_mode == SET_IO_MAPPED) {
-    if (d.type == SET_JOB_MLP_LN) {
-      *why = "SET_IO_MAPPED: MLP inputs feed TMA loads and must be in device memory (use SET_IO_HOST)";
-      return SET_EINVAL;
-    }
-    if (!dev_->io_accessible(d.in) || !dev_->io_accessible(d.out)) {
-      *why = "SET_IO_MAPPED: in/out must be page-locked host memory (or device memory) the GPU can address";
-      return SET_EINVAL;
-    }
+  if (io_maps_in(cfg_.io_mode) && d.type == SET_JOB_MLP_LN) {
+    *why = "mapped input: MLP inputs feed TMA loads and must be copied into device memory";
+    return SET_EINVAL;
+  }
+  if ((io_maps_in(cfg_.io_mode) && !dev_->io_accessible(d.in)) ||
+      (io_maps_out(cfg_.io_mode) && !dev_->io_accessible(d.out))) {
+    *why = "mapped I/O: in/out must be page-locked host memory (or device memory) the GPU can address";
+    return SET_EINVAL;
   }
   const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);
   if (use_arena_) {
@@ -633,7 +632,8 @@ void Executor::reset_stats() {
 
 set_status Executor::run_baseline(int kind, const set_job_desc* jobs, size_t n, set_stats_t* out) {
   if (!jobs || !out) return SET_EINVAL;
-  if (cfg_.io_mode == SET_IO_MAPPED) return fail(SET_EINVAL, "baselines copy with cudaMemcpyAsync: use SET_IO_HOST");
+  if (io_maps_in(cfg_.io_mode) || io_maps_out(cfg_.io_mode))
+    return fail(SET_EINVAL, "baselines copy with cudaMemcpyAsync: use SET_IO_HOST");
   if (sticky_.load() != SET_OK) return (set_status)sticky_.load();
   const set_status w = wait_all(60 * 1000000ll);
   if (w != SET_OK) return w;

@@ -89,6 +89,10 @@ class Device {
                                   uint64_t* t1_ns, std::string* err) = 0;
 };
 
+// Which side of a job the kernels read / write in host memory themselves (no copy node).
+inline bool io_maps_in(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_IN; }
+inline bool io_maps_out(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_OUT; }
+
 // Product CUDA device; the host-simulation test library links its own factory instead.
 std::unique_ptr<Device> make_device(const set_config& cfg);
 

@@ -11,16 +11,16 @@ from gpu_util import (S, blur_job, check_blur, check_hot, check_img, check_scan,
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cb_mode", [0, 3])
-def test_mapped_io_all_copyless_types(cb_mode):
+@pytest.mark.parametrize("cb_mode,io", [(0, "MAPPED"), (3, "MAPPED"), (3, "MAPPED_IN"), (3, "MAPPED_OUT")])
+def test_mapped_io_all_copyless_types(cb_mode, io):
     s = S()
     jobs = ([blur_job(k) for k in range(4)] + [blur_job(50, W=17, H=3)] +
             [scan_job(100 + k, n=65536 - 999 * k) for k in range(4)] +
             [img_job(200 + k, dims=d) for k, d in enumerate([(300, 200), (129, 1), (1, 70), (640, 480)])] +
             [hot_job(300, R=37, C=100, K=13), hot_job(301, R=512, C=512, K=64)])
     slot = max(s.set_job_slot_bytes(j.type, s.dims4(*j.dims)) for j in jobs)
-    st = run_jobs(jobs, num_streams=3, num_workers=2, ring_depth=2, slot_bytes=slot, io_mode=s.SET_IO_MAPPED,
-                  cb_mode=cb_mode)
+    st = run_jobs(jobs, num_streams=3, num_workers=2, ring_depth=2, slot_bytes=slot,
+                  io_mode=getattr(s, "SET_IO_" + io), cb_mode=cb_mode)
     assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
     for j in jobs:
         {1: check_blur, 2: check_scan, 3: check_img, 5: check_hot}[j.type](j)
@@ -58,3 +58,16 @@ def test_mapped_io_refuses_batches_and_baselines():
         assert s.set_run_baseline(ctx, s.SET_BASE_BATCH_SYNC, arr, 1, ctypes.byref(st)) == s.SET_EINVAL
     finally:
         s.set_destroy(ctx)
+
+
+def test_mapped_output_mlp():
+    # outputs stored by the kernels into host memory; x still copied (it feeds TMA loads)
+    from gpu_util import check_mlp
+    s = S()
+    jobs = [mlp_job(600 + k, m=m) for k, m in enumerate([1, 77, 128, 200, 256])]
+    slot = s.set_job_slot_bytes(s.SET_JOB_MLP_LN, s.dims4(256))
+    st = run_jobs(jobs, num_streams=2, num_workers=1, slot_bytes=slot, io_mode=s.SET_IO_MAPPED_OUT, cb_mode=3)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        check_mlp(j)
+    check_trailers(jobs)
