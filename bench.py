@@ -918,7 +918,7 @@ def run_workload(args, d: Dist):
         cfg = dict(common, num_streams=16, ring_depth=4, cb_every=1, slot_bytes=64 << 20, arena_bytes=8 << 30)
         line["config"] = {"arrivals_per_rate": npool, "mix": "40% blur 256x256, 40% image (log-uniform sides), "
                           "20% MLP (m 1..256)", "arena_bytes": 8 << 30, "streams": 16, "ring_depth": 4,
-                          "workers": 1}
+                          "workers": "2 (polled arms), 1 (host-callback arm)"}
         sweep = []
         for lam in rates:
             ts, kinds, _ = datagen.serve_trace(lam, npool)
@@ -929,14 +929,16 @@ def run_workload(args, d: Dist):
                 used[int(k)] += 1
             off = (ctypes.c_uint64 * npool)(*[int(x * 1e9) for x in ts])
             row = {"rate": lam}
-            # set: completion by the polling thread (cb_mode 3); set_host_callbacks: Algorithm 3's
+            # set: the request loop binds and launches an arrival itself when a slot and its memory
+            # are free (bind_at_submit 2; otherwise a dispatch thread does when one frees up),
+            # completion by the polling thread (cb_mode 3); set_dispatch_threads: every arrival is
+            # queued and launched by a dispatch thread; set_host_callbacks: that, with Algorithm 3's
             # host function on the lane stream (cb_mode 1)
-            # set_launch_at_submit: the request loop binds and launches an arrival itself when a slot
-            # and its memory are free (bind_at_submit 2), no hand-off to a dispatch thread
-            for name, mode, cbm, bind in (("set", S.SET_SERVE_SET, 3, 0), ("set_launch_at_submit", S.SET_SERVE_SET, 3, 2),
-                                          ("set_host_callbacks", S.SET_SERVE_SET, 1, 0),
-                                          ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1, 0)):
-                ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm, bind_at_submit=bind)))
+            for name, mode, cbm, bind, nw in (("set", S.SET_SERVE_SET, 3, 2, 2),
+                                              ("set_dispatch_threads", S.SET_SERVE_SET, 3, 0, 2),
+                                              ("set_host_callbacks", S.SET_SERVE_SET, 1, 0, 1),
+                                              ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1, 0, 1)):
+                ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm, bind_at_submit=bind, num_workers=nw)))
                 st = S.set_stats_t()
                 with clocks.window():
                     S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)

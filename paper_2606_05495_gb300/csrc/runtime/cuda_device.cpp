@@ -406,6 +406,7 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   }
   gi.nk = nk;
   SET_CK(cudaGraphInstantiate(&gi.exec, gi.graph, 0));
+  SET_CK(cudaGraphUpload(gi.exec, lanes_[s.lane]));  // device-side setup now, not at the first job
   return SET_OK;
 }
 
@@ -575,6 +576,7 @@ set_status CudaDevice::build_batch_graph(Slot& s, uint32_t type, std::string* er
                                     256, kind_out_));
   bg.nk = nk;
   SET_CK(cudaGraphInstantiate(&bg.exec, bg.graph, 0));
+  SET_CK(cudaGraphUpload(bg.exec, lanes_[s.lane]));
   return SET_OK;
 }
 
@@ -847,8 +849,7 @@ set_status CudaDevice::run_baseline(int kind, const JobRec* jobs, size_t n, std:
     *t0 = now_ns();
     for (size_t i = 0; i < n && result == SET_OK; ++i) {
       const JobRec& j = jobs[i];
-      while (j.d.t_arrival_ns && now_ns() < j.d.t_arrival_ns) {
-      }
+      if (j.d.t_arrival_ns) wait_until_ns(j.d.t_arrival_ns);
       setk::JobLayout Lo;
       setk::KernelLaunch kl[setk::kMaxKernels];
       int nk = 0;
@@ -880,8 +881,7 @@ set_status CudaDevice::run_baseline(int kind, const JobRec* jobs, size_t n, std:
     size_t base = 0;
     while (base < n && result == SET_OK) {
       const uint64_t first = jobs[base].d.t_arrival_ns;
-      while (first && now_ns() < first) {
-      }
+      if (first) wait_until_ns(first);
       size_t nb = 1;
       const uint64_t now = now_ns();
       while (nb < L && base + nb < n && jobs[base + nb].d.t_arrival_ns <= now) ++nb;

@@ -690,8 +690,7 @@ set_status Executor::serve(int mode, const set_job_desc* jobs, const uint64_t* a
   reset_stats();
   for (size_t i = 0; i < n; ++i) {
     const uint64_t target = t0 + arrival_ns[i];
-    while (now_ns() < target) {
-    }
+    wait_until_ns(target);
     set_job_desc d = jobs[i];
     d.t_arrival_ns = target;
     d.flags &= ~SET_F_NONBLOCK;

@@ -29,6 +29,20 @@ inline uint64_t now_ns() {
   return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
 }
 
+// Request loops: returns at `target` (CLOCK_MONOTONIC ns).  Sleeps while more than 150 us remain,
+// then spins, so a loop waiting for sparse arrivals does not hold a core.
+inline void wait_until_ns(uint64_t target) {
+  for (uint64_t t = now_ns(); t + 150000ull < target; t = now_ns()) {
+    const uint64_t d = target - t - 100000ull;
+    timespec ts;
+    ts.tv_sec = (time_t)(d / 1000000000ull);
+    ts.tv_nsec = (long)(d % 1000000000ull);
+    nanosleep(&ts, nullptr);
+  }
+  while (now_ns() < target) {
+  }
+}
+
 class Signal {
  public:
   uint32_t load() const { return seq_.load(std::memory_order_seq_cst); }
