@@ -226,8 +226,15 @@ void CudaDevice::poll_main() {
       }
     }
     if (waiting) {
-      // jobs in flight: poll again at once, yielding the core after a run of empty rounds
+      // jobs in flight: after a round without a completion, pause 2 us (a plain clock spin, no
+      // driver call) before querying again, so the queries do not contend with the dispatch
+      // threads' launches for the driver; yield the core after a run of empty rounds
       idle_rounds = progressed ? 0 : idle_rounds + 1;
+      if (!progressed) {
+        const uint64_t t_next = now_ns() + 2000ull;
+        while (now_ns() < t_next && poll_sig_.load() == seen) {
+        }
+      }
       if (idle_rounds > 64) std::this_thread::yield();
       continue;
     }
