@@ -66,3 +66,32 @@ def test_autotuner_picks_a_candidate_and_results_stay_exact(type_):
     for j in sample:
         check(j)
     check_trailers(sample)
+
+
+@pytest.mark.parametrize("type_", [3, 4])
+def test_batched_form_in_its_bench_configuration(type_):
+    # the launch configuration bench.py times for the batched form: 16 lanes x 2 slots, polled
+    # completion, autotuned batches of up to 16 in an 8 GiB arena, the workload's own sizes
+    import ctypes
+    s = S()
+    n = 160
+    jobs = [img_job(k) for k in range(n)] if type_ == 3 else [mlp_job(k) for k in range(n)]
+    ctx = s.create(s.default_config(num_streams=16, num_workers=1, ring_depth=2, cb_mode=3, batch_max=16,
+                                    arena_bytes=8 << 30, slot_bytes=1 << 30))
+    try:
+        arr = (s.set_job_desc * n)(*[j.desc for j in jobs])
+        r = s.set_tune_result()
+        s.check(s.set_autotune(ctx, type_, arr, 64, ctypes.byref(r)), "set_autotune", ctx)
+        first = ctypes.c_uint64()
+        s.check(s.set_submit_many(ctx, arr, n, ctypes.byref(first), None), "submit", ctx)
+        s.check(s.set_wait_all(ctx, 120_000_000), "wait", ctx)
+        st = s.set_stats_t()
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "stats", ctx)
+        assert st.completed == n and st.failed == 0 and st.canary_errors == 0
+        for k, j in enumerate(jobs):
+            j.id = first.value + k
+    finally:
+        s.set_destroy(ctx)
+    for j in jobs:
+        (check_img if type_ == 3 else check_mlp)(j)
+    check_trailers(jobs)

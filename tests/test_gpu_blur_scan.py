@@ -39,6 +39,18 @@ def test_scan_config_4096_jobs_8_streams_stealing():
     check_trailers(jobs)
 
 
+def test_scan_headline_launch_configuration():
+    # the configuration bench.py times: 4096 full-size jobs, 16 lanes x 4 slots, 4 dispatch threads,
+    # polled completion, stealing; every job checked against the oracle
+    jobs = [scan_job(j) for j in range(4096)]
+    st = run_jobs(jobs, timeout_s=300, num_streams=16, num_workers=4, ring_depth=4, cb_mode=3,
+                  slot_bytes=S().set_job_slot_bytes(2, S().dims4(65536)))
+    assert st["completed"] == 4096 and st["failed"] == 0 and st["canary_errors"] == 0
+    for j in jobs:
+        check_scan(j)
+    check_trailers(jobs)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 4095, 4096, 4097, 65537, 100003, 1 << 20])
 def test_scan_edge_sizes(n):
     jobs = [scan_job(k, n=n) for k in range(3)]
