@@ -16,7 +16,9 @@
  *     and chain a completion callback to it (Algorithm 2);
  *   - the completion callback, run by the CUDA driver through cudaLaunchHostFunc after an event
  *     recorded behind the graph, counts the job done and returns the slot to W_pool
- *     (Algorithm 3).  The lane stream itself never waits on the host.
+ *     (Algorithm 3).  The lane stream itself never waits on the host.  set_config.cb_mode 3
+ *     runs the same completion code on a thread of the context that polls each lane's oldest
+ *     event instead (an addition: lower latency than the driver's callback thread).
  *
  * Conventions (every function):
  *   - The return value is the status; nothing throws across this boundary.
@@ -233,7 +235,11 @@ set_status set_create_ex(const set_config* cfg, set_ctx** out);
 
 /* Job submitter (Algorithm 1): validate, claim the next id, push to the shortest non-full lane
  * queue (lowest index on ties).  Blocks while every queue is full unless SET_F_NONBLOCK.
- * *job_id (may be NULL) receives the id echoed in the trailer. */
+ * *job_id (may be NULL) receives the id echoed in the trailer.  With set_config.bind_at_submit
+ * the calling thread first tries to take a free slot (and, with an arena, the job's memory block):
+ * on success it rebinds the slot's graph to the job (UpdateGraphParams) and queues the slot bound
+ * (1) or launches it itself (2); a launch error then completes the job with that status.  The
+ * calling thread must be able to make the context's device current (it is restored after). */
 set_status set_submit(set_ctx* ctx, const set_job_desc* job, uint64_t* job_id);
 
 /* Submits n jobs in order (same rules as set_submit, one call across the boundary).
