@@ -162,7 +162,8 @@ size_t Executor::job_block_bytes(const set_job_desc& d) {
   return L.end;
 }
 
-// Algorithm 1 (job submitter): claim an id, push to the shortest queue that is not full.
+// Algorithm 1 (job submitter): claim an id, push to the shortest queue that is not full; with
+// bind_at_submit, first try to bind the job to a free slot here (and launch it, mode 2).
 set_status Executor::submit(const set_job_desc* d, uint64_t* id_out) {
   if (!d) return SET_EINVAL;
   if (stop_.load()) return SET_ESHUTDOWN;
@@ -298,8 +299,8 @@ bool Executor::find_job(uint32_t lane, JobRec& j, bool& stolen) {
   return false;
 }
 
-// Algorithm 2, dispatcher loop: pop a free slot (W_pool), FindJob, LaunchJob.  Waiting is a
-// futex sleep on the pool / submit signals, never a poll.
+// Closes every open completion group of this dispatcher (AddCallback on its last slot): done
+// before the dispatcher waits, so that no launched job is left without a completion.
 void Executor::flush_groups(std::vector<Slot*>& pending, std::vector<int>& count) {
   for (size_t l = 0; l < pending.size(); ++l) {
     if (!pending[l]) continue;
@@ -314,6 +315,9 @@ void Executor::flush_groups(std::vector<Slot*>& pending, std::vector<int>& count
   }
 }
 
+// Algorithm 2, dispatcher loop: launch a slot bound at submit if one is ready; else pop a free
+// slot (W_pool), FindJob, UpdateGraphParams, LaunchJob.  Waiting is a spin, then a futex sleep on
+// the pool / submit signals; the device is never polled here.
 void Executor::worker_main(int) {
   dev_->thread_init();
   const uint64_t spin_ns = (uint64_t)cfg_.spin_us * 1000ull;
