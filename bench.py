@@ -3,7 +3,7 @@
 
 Workload (the headline configuration): 4096 scan jobs, each saxpy -> exclusive prefix sum ->
 max|S| over n = 65536 fp32 elements (x, y uniform [-1, 1), per-job a uniform [-2, 2)), 512 KiB
-copied in and 512 KiB + 32 B copied out per job, 16 lane streams with rings of 4 slots, four host
+copied in and 512 KiB + 32 B copied out per job, 8 lane streams with rings of 4 slots, four host
 dispatch threads, work stealing, completion detected by a thread polling each lane's oldest event.  A step is one pass of all 4096 jobs through the executor (submit, dispatch, graph
 launch, H2D copy, kernel, D2H copy, completion callback) until set_wait_all returns.
 
@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["set", "reference"], default="set")
     p.add_argument("--jobs", type=int, default=4096)
-    p.add_argument("--streams", type=int, default=16)
+    p.add_argument("--streams", type=int, default=8, help="lanes (the scan configuration names 8 streams)")
     p.add_argument("--workers", type=int, default=4, help="host dispatch threads")
     p.add_argument("--ring", type=int, default=4)
     p.add_argument("--cb-mode", type=int, default=3, help="completion path (set_config.cb_mode); 3 = polled events")

@@ -210,6 +210,9 @@ typedef struct {
   double mean_service_us;   /* launching starts -> the job's completion is handled on the
                                host: parameter updates and launch calls, device time, callback
                                delivery */
+  double mean_kernel_gap_us; /* mean gap between consecutive kernels on the device timeline, from
+                               the last CUPTI trace (set_trace_start / set_trace_stop) that began
+                               after the last set_reset_stats; NaN when there is none */
 } set_stats_t;
 
 /* ---- sizes ---- */

@@ -58,7 +58,7 @@ class set_stats_t(ctypes.Structure):
                 ("jobs_per_s", c_double), ("p50_us", c_double), ("p99_us", c_double), ("max_us", c_double),
                 ("mean_update_us", c_double), ("mean_launch_us", c_double), ("mem_waits", c_uint64),
                 ("order_errors", c_uint64), ("arena_peak_bytes", c_uint64),
-                ("mean_queue_us", c_double), ("mean_service_us", c_double)]
+                ("mean_queue_us", c_double), ("mean_service_us", c_double), ("mean_kernel_gap_us", c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -4,6 +4,7 @@
 #include "executor.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "layout.h"
@@ -11,6 +12,9 @@
 namespace setrt {
 
 namespace {
+std::mutex g_trace_mu;
+double g_trace_gap_us = 0.0;
+uint64_t g_trace_start_ns = 0;  // 0: no trace yet
 
 void normalize(set_config& c) {
   if (c.ring_depth <= 0) c.ring_depth = 2;
@@ -38,6 +42,19 @@ bool spin_until(F ready, uint64_t spin_ns) {
 }  // namespace
 
 Executor::Executor(const set_config& cfg) : cfg_(cfg) {}
+
+void note_trace_gap(double gap_us, uint64_t t_start_ns) {
+  std::lock_guard<std::mutex> g(g_trace_mu);
+  g_trace_gap_us = gap_us;
+  g_trace_start_ns = t_start_ns;
+}
+
+bool last_trace_gap(uint64_t since_ns, double* gap_us) {
+  std::lock_guard<std::mutex> g(g_trace_mu);
+  if (g_trace_start_ns == 0 || g_trace_start_ns < since_ns) return false;
+  *gap_us = g_trace_gap_us;
+  return true;
+}
 
 set_status Executor::create(const set_config& cfg_in, Executor** out, std::string* err) {
   set_config cfg = cfg_in;
@@ -73,6 +90,7 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
     ex->use_arena_ = true;
   }
   ex->batch_limit_.store(cfg.batch_max);
+  ex->t_reset_ns_.store(now_ns());
   for (uint32_t i = 0; i < L; ++i) ex->queues_.emplace_back(new MpmcRing<JobRec>((size_t)cfg.queue_capacity));
   ex->free_.reset(new MpmcRing<uint32_t>((size_t)L * R));
   if (cfg.bind_at_submit) ex->ready_.reset(new MpmcRing<uint32_t>((size_t)L * R));
@@ -612,6 +630,8 @@ void Executor::stats(set_stats_t* s) const {
   const uint64_t nt = timed_jobs_.load();
   s->mean_queue_us = nt ? (double)queue_ns_.load() * 1e-3 / (double)nt : 0.0;
   s->mean_service_us = nt ? (double)service_ns_.load() * 1e-3 / (double)nt : 0.0;
+  double gap = 0.0;
+  s->mean_kernel_gap_us = last_trace_gap(t_reset_ns_.load(), &gap) ? gap : std::nan("");
 }
 
 void Executor::reset_stats() {
@@ -630,6 +650,7 @@ void Executor::reset_stats() {
   timed_jobs_.store(0);
   order_errors_.store(0);
   t_first_ns_.store(0);
+  t_reset_ns_.store(now_ns());
   t_last_ns_.store(0);
   lat_.reset();
 }

@@ -89,6 +89,11 @@ class Device {
                                   uint64_t* t1_ns, std::string* err) = 0;
 };
 
+// The last CUPTI trace's mean kernel gap (process-wide): written by set_trace_stop, read by the
+// contexts' statistics when the trace began after their last reset.
+void note_trace_gap(double gap_us, uint64_t t_start_ns);
+bool last_trace_gap(uint64_t since_ns, double* gap_us);
+
 // Which side of a job the kernels read / write in host memory themselves (no copy node).
 inline bool io_maps_in(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_IN; }
 inline bool io_maps_out(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_OUT; }
@@ -156,6 +161,7 @@ class Executor {
   std::atomic<uint64_t> update_ns_{0}, launch_ns_{0}, launched_{0};
   std::atomic<uint64_t> queue_ns_{0}, service_ns_{0}, timed_jobs_{0};  // latency breakdown
   std::atomic<uint64_t> t_first_ns_{0}, t_last_ns_{0};
+  std::atomic<uint64_t> t_reset_ns_{0};  // last reset of the statistics (creation)
   std::atomic<uint64_t> stat_base_submitted_{0}, stat_base_done_{0}, stat_base_failed_{0};
   std::atomic<uint64_t> mem_waits_{0};
   std::atomic<uint64_t> order_errors_{0};

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "executor.h"
 #include "set.h"
 #include "thread_error.h"
 
@@ -41,6 +42,7 @@ std::mutex g_mu;
 Cupti g_c;
 std::vector<Rec> g_recs;
 bool g_on = false;
+uint64_t g_start_ns = 0;  // host clock at set_trace_start
 
 bool load_cupti() {
   if (g_c.ok) return true;
@@ -125,6 +127,7 @@ extern "C" set_status set_trace_start(void) {
     return SET_ECUDA;
   }
   g_on = true;
+  g_start_ns = setrt::now_ns();
   return SET_OK;
 }
 
@@ -174,6 +177,7 @@ extern "C" set_status set_trace_stop(set_trace_summary* out) {
     run_end = std::max(run_end, kiv[i].second);
   }
   out->mean_kernel_gap_us = kiv.size() > 1 ? gsum / (double)(kiv.size() - 1) * 1e-3 : 0.0;
+  setrt::note_trace_gap(out->mean_kernel_gap_us, g_start_ns);
   out->max_kernel_gap_us = gmax * 1e-3;
   double best = -1;
   double ksum = 0;

@@ -200,3 +200,31 @@ def test_bounded_device_wait_reports_and_context_survives():
     for k in (0, 1, 3, 4):
         assert jobs[k].status.value == s.SET_OK
         check_scan(jobs[k])
+
+
+def test_stats_carry_the_traced_kernel_gap():
+    import math
+    s = S()
+    jobs = [scan_job(1200 + k, n=65536) for k in range(64)]
+    slot = s.set_job_slot_bytes(s.SET_JOB_SAXPY_SCAN_MAX, s.dims4(65536))
+    ctx = s.create(s.default_config(num_streams=4, num_workers=2, ring_depth=2, slot_bytes=slot, cb_mode=3))
+    try:
+        st = s.set_stats_t()
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "stats", ctx)
+        assert math.isnan(st.mean_kernel_gap_us)
+        arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+        tr = s.set_trace_summary()
+        if s.set_trace_start() != s.SET_OK:
+            pytest.skip("CUPTI activity tracing unavailable")
+        s.check(s.set_submit_many(ctx, arr, len(jobs), None, None), "submit", ctx)
+        s.check(s.set_wait_all(ctx, 60_000_000), "wait", ctx)
+        s.check(s.set_trace_stop(ctypes.byref(tr)), "trace stop")
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "stats", ctx)
+        assert tr.kernels == len(jobs) and st.mean_kernel_gap_us == tr.mean_kernel_gap_us >= 0
+        s.check(s.set_reset_stats(ctx), "reset", ctx)
+        s.check(s.set_stats(ctx, ctypes.byref(st)), "stats", ctx)
+        assert math.isnan(st.mean_kernel_gap_us)  # the trace began before the reset
+    finally:
+        s.set_destroy(ctx)
+    for j in jobs:
+        check_scan(j)
