@@ -95,6 +95,9 @@ typedef enum {
 
 /* set_job_desc.flags */
 #define SET_F_NONBLOCK 0x1u /* set_submit returns SET_EAGAIN instead of waiting for queue room */
+#define SET_F_TEST_GUARD 0x200u /* test hook for set_config.guards: the guard-arming kernel writes one
+                                   wrong byte into the band after `out`, so the check must report
+                                   SET_DEVERR_GUARD for this job (no kernel touches the band) */
 #define SET_F_TEST_STALL 0x100u /* test hook for failure detection without a GPU fault: in a scan
                                    job of >= 3 tiles, tile 1 exits without publishing, so tile 2's
                                    look-back and the final max gather wait until their bounded
@@ -110,6 +113,7 @@ typedef struct {
 
 #define SET_TRAILER_MAGIC 0x5E7Cu
 #define SET_DEVERR_WAIT 0x1u /* a bounded device-side wait gave up */
+#define SET_DEVERR_GUARD 0x2u /* set_config.guards: a guard band next to the job's regions changed */
 
 typedef struct {
   uint32_t type;          /* set_job_type */
@@ -190,6 +194,14 @@ typedef struct {
                           so an idle executor starts a job without waking a dispatch thread.  With
                           arena_bytes the job is bound at submit only if its block is free then.
                           Not with batch_max > 1. */
+  int guards;          /* 1: bounds check of the stage kernels (a test instrument; compute-sanitizer
+                          is not available): each job's in, out and scratch regions in its slot are
+                          followed, and `in` preceded, by 256-byte guard bands that a kernel writes
+                          with a pattern before the job's H2D copy and another checks after its last
+                          stage kernel; a changed band sets SET_DEVERR_GUARD in the trailer and the
+                          job completes with SET_EDEVICE.  Slots need kGuardBytes * 4 + 1 KiB more
+                          than set_job_slot_bytes.  SET_IO_HOST (the host reads the trailer), per-job
+                          graphs only (not with arena_bytes or batch_max > 1).  Default 0. */
 } set_config;
 
 typedef struct {

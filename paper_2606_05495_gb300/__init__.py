@@ -24,11 +24,13 @@ STATUS_NAMES = {0: "SET_OK", -1: "SET_EINVAL", -2: "SET_ENOMEM", -3: "SET_EAGAIN
 SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX, SET_JOB_IMG_SOBEL_HIST, SET_JOB_MLP_LN, SET_JOB_HOTSPOT = 1, 2, 3, 4, 5
 SET_F_NONBLOCK = 0x1
 SET_F_TEST_STALL = 0x100
+SET_F_TEST_GUARD = 0x200
 SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED, SET_IO_MAPPED_IN, SET_IO_MAPPED_OUT = 0, 1, 2, 3, 4
 SET_BASE_SYNC, SET_BASE_BATCH_SYNC = 1, 2
 SET_SERVE_SET, SET_SERVE_BATCH_SYNC = 0, 1
 SET_TRAILER_MAGIC = 0x5E7C
 SET_DEVERR_WAIT = 0x1
+SET_DEVERR_GUARD = 0x2
 
 
 class set_trailer(ctypes.Structure):
@@ -49,7 +51,7 @@ class set_config(ctypes.Structure):
                 ("pool", c_void_p), ("pool_bytes", c_size_t), ("type_mask", c_uint32), ("device", c_int),
                 ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int), ("cb_every", c_int),
                 ("batch_max", c_int), ("img_ctas_per_sm", c_int), ("img_tile", c_int), ("stamps", c_int),
-                ("arena_bytes", c_size_t), ("bind_at_submit", c_int)]
+                ("arena_bytes", c_size_t), ("bind_at_submit", c_int), ("guards", c_int)]
 
 
 class set_stats_t(ctypes.Structure):

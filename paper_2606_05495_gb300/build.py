@@ -23,7 +23,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_sobel_hist.cu",
-              "kernels/mlp_ln.cu", "kernels/hotspot.cu", "kernels/plan.cu"]
+              "kernels/mlp_ln.cu", "kernels/hotspot.cu", "kernels/guards.cu", "kernels/plan.cu"]
 CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp",
                "runtime/trace.cpp"]
 HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "kernels/cp_async.cuh", "runtime/executor.h", "runtime/sync.h",

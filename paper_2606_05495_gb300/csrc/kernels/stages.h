@@ -102,6 +102,10 @@ bool plan_img_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
 bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_t* d_block, uint8_t* h_table,
                     uint32_t slot_gen, const void* w1, const void* w2, KernelLaunch* kl, int* nk);
 
+// set_config.guards: the arming and checking kernels of a job placed with place_job_guarded in
+// the slot at slot_base (plant: the SET_F_TEST_GUARD hook).
+void plan_guards(uint8_t* slot_base, const JobLayout& L, bool plant, KernelLaunch* arm, KernelLaunch* check);
+
 // One-time function attributes (dynamic shared memory limits, cluster sizes).
 cudaError_t kernels_init();
 cudaError_t blur_hist_init();

@@ -36,6 +36,7 @@ struct GraphInst {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t h2d = nullptr, d2h = nullptr;
+  cudaGraphNode_t arm = nullptr, check = nullptr;  // set_config.guards: guard bands around the job
   cudaGraphNode_t kn[setk::kMaxKernels] = {};
   int nk = 0;
 };
@@ -338,7 +339,10 @@ set_status CudaDevice::init(const set_config& cfg, std::vector<Slot>& slots, std
 bool CudaDevice::plan(const Slot& s, const JobRec& j, setk::JobLayout* L, setk::KernelLaunch* kl, int* nk) const {
   if (!setk::job_sizes(j.d.type, j.d.dims, L)) return false;
   uint8_t* base = s.job_mem ? s.job_mem : s.dev;
-  setk::place_job(L, s.job_mem ? 0 : ctl_);
+  if (cfg_.guards)
+    setk::place_job_guarded(L, s.job_mem ? 0 : ctl_);
+  else
+    setk::place_job(L, s.job_mem ? 0 : ctl_);
   setk::JobPlanIn in;
   in.type = j.d.type;
   in.flags = j.d.flags;
@@ -377,14 +381,24 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   const bool copy_in = !io_maps_in(cfg_.io_mode), copy_out = !io_maps_out(cfg_.io_mode);
   const void* src_ph = cfg_.io_mode == SET_IO_DEVICE ? ph_dev_ : ph_host_;
   void* dst_ph = cfg_.io_mode == SET_IO_DEVICE ? ph_dev_ : ph_host_;
+  setk::KernelLaunch gk[2];
+  if (cfg_.guards) {  // arm the bands first: the H2D copy must not touch them either
+    setk::plan_guards(base, L, false, &gk[0], &gk[1]);
+    const cudaKernelNodeParams p = node_params(gk[0]);
+    SET_CK(cudaGraphAddKernelNode(&gi.arm, gi.graph, nullptr, 0, &p));
+  }
   if (copy_in)
-    SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, nullptr, 0, base + L.in_off, src_ph, L.in_bytes, kind_in_));
+    SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, gi.arm ? &gi.arm : nullptr, gi.arm ? 1 : 0, base + L.in_off,
+                                    src_ph, L.in_bytes, kind_in_));
   uint32_t has_dependents = 0;
   for (int k = 0; k < nk; ++k) {
     cudaGraphNode_t deps[setk::kMaxKernels];
     size_t nd = 0;
     if (kl[k].deps == 0) {
-      if (copy_in) deps[nd++] = gi.h2d;
+      if (copy_in)
+        deps[nd++] = gi.h2d;
+      else if (gi.arm)
+        deps[nd++] = gi.arm;
     } else {
       for (int q = 0; q < k; ++q)
         if (kl[k].deps & (1u << q)) {
@@ -399,6 +413,12 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   size_t ns = 0;
   for (int k = 0; k < nk; ++k)
     if (!(has_dependents & (1u << k))) sinks[ns++] = gi.kn[k];
+  if (cfg_.guards) {  // check after every stage kernel, before the D2H copy returns the trailer
+    const cudaKernelNodeParams p = node_params(gk[1]);
+    SET_CK(cudaGraphAddKernelNode(&gi.check, gi.graph, sinks, ns, &p));
+    sinks[0] = gi.check;
+    ns = 1;
+  }
   if (copy_out)
     SET_CK(cudaGraphAddMemcpyNode1D(&gi.d2h, gi.graph, sinks, ns, dst_ph, base + L.out_off, L.out_bytes, kind_out_));
   if (cfg_.cb_mode == 2) {  // Algorithm 3's callback as the graph's last node, bound to this slot
@@ -442,6 +462,17 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
     }
   if (e == cudaSuccess && copy_out)
     e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.d2h, j.d.out, base + L.out_off, L.out_bytes, kind_out_);
+  if (e == cudaSuccess && gi.arm) {
+    setk::KernelLaunch gk[2];
+    setk::plan_guards(base, L, (j.d.flags & SET_F_TEST_GUARD) != 0, &gk[0], &gk[1]);
+    cudaKernelNodeParams p = node_params(gk[0]);
+    e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.arm, &p);
+    if (e == cudaSuccess) {
+      p = node_params(gk[1]);
+      e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.check, &p);
+    }
+    cost->updates += 2;
+  }
   cost->update_ns += now_ns() - t0;
   cost->updates += (uint64_t)nk + (copy_in ? 1 : 0) + (copy_out ? 1 : 0);
   if (e != cudaSuccess) {

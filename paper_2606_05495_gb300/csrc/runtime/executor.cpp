@@ -63,9 +63,11 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
       cfg.io_mode < SET_IO_HOST || cfg.io_mode > SET_IO_MAPPED_OUT || cfg.cb_mode < 0 || cfg.cb_mode > 3 ||
       ((io_maps_in(cfg.io_mode) || io_maps_out(cfg.io_mode)) && cfg.batch_max > 1) ||
-      cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1)) {
+      cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1) ||
+      (cfg.guards && (cfg.arena_bytes || cfg.batch_max > 1 || cfg.io_mode != SET_IO_HOST))) {
     *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
-           "cb_mode 0..3, no batched form with mapped I/O or bind_at_submit)";
+           "cb_mode 0..3, no batched form with mapped I/O or bind_at_submit; guards only with SET_IO_HOST, "
+           "without arena or batches)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -165,7 +167,10 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
     }
     return SET_OK;
   }
-  setk::place_job(&L, ctl);
+  if (cfg_.guards)
+    setk::place_job_guarded(&L, ctl);
+  else
+    setk::place_job(&L, ctl);
   if (L.end > cfg_.slot_bytes || setk::control_offset(d.type) + L.persist_bytes > ctl) {
     *why = "job does not fit the slot (slot_bytes too small)";
     return SET_ENOMEM;

@@ -82,6 +82,20 @@ size_t control_offset(uint32_t type) {
   }
 }
 
+void place_job_guarded(JobLayout* L, size_t ctl) {
+  L->in_off = align256(ctl) + kGuardBytes;
+  L->out_off = align256(L->in_off + L->in_bytes + kGuardBytes);
+  L->scratch_off = align256(L->out_off + L->out_bytes + kGuardBytes);
+  L->end = align256(L->scratch_off + L->scratch_bytes + kGuardBytes);
+}
+
+void guard_offsets(const JobLayout& L, size_t off[4]) {
+  off[0] = L.in_off - kGuardBytes;
+  off[1] = L.in_off + L.in_bytes;
+  off[2] = L.out_off + L.out_bytes;
+  off[3] = L.scratch_off + L.scratch_bytes;
+}
+
 void place_job(JobLayout* L, size_t ctl) {
   L->in_off = ctl;
   L->out_off = L->in_off + align256(L->in_bytes);

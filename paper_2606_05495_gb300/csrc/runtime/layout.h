@@ -31,6 +31,13 @@ size_t control_offset(uint32_t type);
 // Places the job's regions after a control block of `ctl` bytes.
 void place_job(JobLayout* L, size_t ctl);
 
+// Guarded placement (set_config.guards): a kGuardBytes band before `in` and one directly after
+// each of in, out and scratch (at in_off + in_bytes etc.); regions still start 256-byte aligned.
+constexpr size_t kGuardBytes = 256;
+void place_job_guarded(JobLayout* L, size_t ctl);
+// The four band offsets of a placed, guarded job.
+void guard_offsets(const JobLayout& L, size_t off[4]);
+
 // ---- batched form: several jobs of one type in one launch ----
 constexpr int kMaxBatch = 64;
 
