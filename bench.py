@@ -66,7 +66,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study"], default="scan",
+    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates"],
+                   default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
     p.add_argument("--clock-ms", type=float, default=25.0, help="clock sampling period in timed regions")
     p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
@@ -744,6 +745,24 @@ def _kernel_only(S, js, n, launches):
     print(json.dumps({"kernel_only": js.kind, "jobs": launches}), flush=True)
 
 
+def run_copy_rates(args, d: Dist):
+    """Pinned host <-> device copy rates (GB/s) by copy size and stream count (set_copy_bandwidth):
+    the copy-engine side of every pipeline bound.  One JSON line per (size, streams)."""
+    import paper_2606_05495_gb300 as S
+    t = _torch()
+    t.cuda.set_device(d.local)
+    for size in (128 << 10, 256 << 10, 512 << 10, 2 << 20, 16 << 20, 64 << 20):
+        for streams in (1, 4, 8, 16, 32):
+            row = {"workload": "copy-rates", "bytes": size, "streams": streams}
+            reps = max(64, min(2048, (512 << 20) // size))
+            for name, dirn in (("h2d_gbs", 0), ("d2h_gbs", 1), ("bidir_total_gbs", 2)):
+                g = ctypes.c_double()
+                S.check(S.set_copy_bandwidth(size, streams, reps, dirn, ctypes.byref(g)), "set_copy_bandwidth")
+                row[name] = g.value
+            if d.rank == 0:
+                print(json.dumps(row), flush=True)
+
+
 def run_bind_study(args, d: Dist):
     """UpdateGraphParams at dispatch vs at submit (set_config.bind_at_submit) on the scan jobs: one
     JSON line per (io mode, completion mode, dispatch threads, bind)."""
@@ -966,6 +985,8 @@ def main():
             run_reference(args, d)
         elif args.workload == "bind-study":
             run_bind_study(args, d)
+        elif args.workload == "copy-rates":
+            run_copy_rates(args, d)
         elif args.workload != "scan":
             run_workload(args, d)
         else:
