@@ -69,6 +69,7 @@ def parse():
     p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates"],
                    default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
+    p.add_argument("--per-stage", action="store_true", help="--kernel-only on images: the three-stage chain")
     p.add_argument("--clock-ms", type=float, default=25.0, help="clock sampling period in timed regions")
     p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
     return p.parse_args()
@@ -732,7 +733,7 @@ def _eq4(line, bound_jobs_per_s):
             if isinstance(v, dict) and v.get("jobs_per_s")}
 
 
-def _kernel_only(S, js, n, launches):
+def _kernel_only(S, js, n, launches, flags=0):
     """Profiling: the stage kernels of `launches` resident jobs alone on one stream, then exit."""
     t = _torch()
     sb = max(S.set_job_scratch_bytes(js.kind, S.dims4(*dd)) for dd in js.dims)
@@ -740,6 +741,7 @@ def _kernel_only(S, js, n, launches):
     st = t.cuda.current_stream().cuda_stream
     for k in range(launches):
         dd = js.descs_dev[k % n]
+        dd.flags |= flags
         S.check(S.set_launch_job(ctypes.byref(dd), dd.in_, dd.out, scratch.data_ptr(), k, 0, st), "set_launch_job")
     t.cuda.synchronize()
     print(json.dumps({"kernel_only": js.kind, "jobs": launches}), flush=True)
@@ -827,7 +829,7 @@ def run_workload(args, d: Dist):
         n = min(args.jobs, 2000)
         js = JobSet(S, kind, range(n), device_copy=bool(args.kernel_only))
         if args.kernel_only:
-            return _kernel_only(S, js, n, args.kernel_only)
+            return _kernel_only(S, js, n, args.kernel_only, S.SET_F_PER_STAGE if args.per_stage else 0)
         sb = js.slot_bytes(S)
         cfg = dict(common, num_streams=16, ring_depth=4, slot_bytes=sb)
         line["config"] = {"jobs": n, "sample_of": 10000 if kind == 3 else 2000, "streams": 16,

@@ -95,6 +95,9 @@ typedef enum {
 
 /* set_job_desc.flags */
 #define SET_F_NONBLOCK 0x1u /* set_submit returns SET_EAGAIN instead of waiting for queue room */
+#define SET_F_PER_STAGE 0x2u /* set_launch_job: run an image job as its three-stage chain (gray,
+                                Gaussian, Sobel + histogram) instead of the fused kernel; contexts
+                                choose with set_config.img_fused */
 #define SET_F_TEST_GUARD 0x200u /* test hook for set_config.guards: the guard-arming kernel writes one
                                    wrong byte into the band after `out`, so the check must report
                                    SET_DEVERR_GUARD for this job (no kernel touches the band) */

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "SET_OK", -1: "SET_EINVAL", -2: "SET_ENOMEM", -3: "SET_EAGAIN
                 -5: "SET_ECUDA", -6: "SET_ESHUTDOWN", -7: "SET_EDEVICE"}
 SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX, SET_JOB_IMG_SOBEL_HIST, SET_JOB_MLP_LN, SET_JOB_HOTSPOT = 1, 2, 3, 4, 5
 SET_F_NONBLOCK = 0x1
+SET_F_PER_STAGE = 0x2
 SET_F_TEST_STALL = 0x100
 SET_F_TEST_GUARD = 0x200
 SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED, SET_IO_MAPPED_IN, SET_IO_MAPPED_OUT = 0, 1, 2, 3, 4

@@ -991,7 +991,8 @@ extern "C" set_status set_launch_job(const set_job_desc* job, const void* d_in, 
   in.d_scratch = static_cast<uint8_t*>(d_scratch) + setk::align256(L.persist_bytes);
   in.job_id = job_id;
   in.slot_gen = slot_gen;
-  in.img_fused = 1;
+  in.img_fused = (job->flags & SET_F_PER_STAGE) ? 0 : 1;
+  in.flags = job->flags;
   setk::KernelLaunch kl[setk::kMaxKernels];
   int nk = 0;
   if (!setk::plan_job(in, kl, &nk)) return SET_EINVAL;

@@ -53,3 +53,23 @@ def test_img_and_scan_and_blur_share_slots():
     for j in jobs:
         {3: check_img, 2: check_scan, 1: check_blur}[j.type](j)
     check_trailers(jobs)
+
+
+@pytest.mark.parametrize("per_stage", [False, True])
+def test_direct_launch_fused_and_per_stage(per_stage):
+    import ctypes
+    from gpu_util import torch
+    s, t = S(), torch()
+    dims = [(700, 33), (129, 257), (1, 1), (640, 480)]
+    jobs = [img_job(300 + k, dims=d, device=True) for k, d in enumerate(dims)]
+    scratch = t.zeros(max(s.set_job_scratch_bytes(3, s.dims4(*j.dims)) for j in jobs), dtype=t.uint8, device="cuda")
+    stream = t.cuda.current_stream().cuda_stream
+    for k, j in enumerate(jobs):
+        if per_stage:
+            j.desc.flags |= s.SET_F_PER_STAGE
+        st = s.set_launch_job(ctypes.byref(j.desc), j.hin.data_ptr(), j.hout.data_ptr(), scratch.data_ptr(), 2000 + k, 0,
+                              stream)
+        assert st == 0
+        t.cuda.synchronize()
+        check_img(j)
+        assert j.trailer()[0] == 2000 + k
