@@ -66,7 +66,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates"],
+    p.add_argument("--lanes", type=int, default=16, help="device-dispatch arm (set_dd): lanes")
+    p.add_argument("--no-dd", action="store_true", help="skip the device-dispatch arm")
+    p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates",
+                                          "dd-study"],
                    default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
     p.add_argument("--per-stage", action="store_true", help="--kernel-only on images: the three-stage chain")
@@ -352,6 +355,66 @@ def timed(S, ctx, descs, n, args, d: Dist, clocks: "Clocks | None" = None):
     return d.max(ms), st.as_dict()
 
 
+def run_step_dd(S, dd, descs, n):
+    done = ctypes.c_size_t()
+    S.dd_check(S.set_dd_submit_many(dd, descs, n, None, ctypes.byref(done)), "set_dd_submit_many", dd)
+    S.dd_check(S.set_dd_wait_all(dd, 600_000_000), "set_dd_wait_all", dd)
+
+
+def timed_dd(S, dd, descs, n, args, d: Dist):
+    """timed() for the device-dispatch lanes (set_dd): W warm-up steps, then K steps between CUDA
+    events with a synchronize on both sides; returns (ms per step, stats, lane graph launches)."""
+    t = _torch()
+    for _ in range(args.warmup):
+        run_step_dd(S, dd, descs, n)
+    S.set_dd_reset_stats(dd)
+    d.barrier()
+    t.cuda.synchronize()
+    e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run_step_dd(S, dd, descs, n)
+    e1.record()
+    t.cuda.synchronize()
+    d.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    st, launches = S.set_stats_t(), ctypes.c_uint64()
+    S.set_dd_stats(dd, ctypes.byref(st), ctypes.byref(launches))
+    return d.max(ms), st.as_dict(), launches.value
+
+
+def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: Dist):
+    """The same scan jobs through set_dd (lane graphs that fetch and run jobs on the device):
+    HBM-resident buffers, then the pinned host buffers read and written in place, then one
+    CUPTI-traced HBM step for the device-timeline gaps."""
+    nj = len(w.ids)
+    dd = S.dd_create(S.dd_default_config(num_lanes=lanes, device=dev_index))
+    try:
+        ms_d, st_d, launches = timed_dd(S, dd, w.descs_dev, nj, args, d)
+        ms_h, st_h, _ = timed_dd(S, dd, w.descs_host, nj, args, d)
+        gap = None
+        tr = S.set_trace_summary()
+        if S.set_trace_start() == S.SET_OK:
+            run_step_dd(S, dd, w.descs_dev, nj)
+            S.set_trace_stop(ctypes.byref(tr))
+            gap = {f: getattr(tr, f) for f in ("kernels", "span_us", "kernel_busy_us", "idle_frac",
+                                                  "mean_kernel_gap_us", "max_kernel_gap_us")}
+    finally:
+        S.set_dd_destroy(dd)
+    world = d.world
+    return {
+        "value": world * nj / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "lanes": lanes,
+        "p50_us": st_d["p50_us"], "p99_us": st_d["p99_us"], "submit_us": st_d["mean_launch_us"],
+        "graph_launches": launches,
+        "e2e_mapped": {"value": world * nj / (ms_h * 1e-3), "unit": UNIT, "ms_per_step": ms_h,
+                       "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
+                       "p50_us": st_h["p50_us"], "p99_us": st_h["p99_us"]},
+        "trace": gap,
+        "note": "set_dd: per lane one graph WHILE {fetch -> SWITCH {scan}} looping on the device; the host "
+                "writes one descriptor per job (no graph update, launch or callback per job)",
+    }
+
+
 def copy_rates(S, job_in: int, job_out: int, streams: int, reps: int = 2048):
     """Pinned copy rates (GB/s) at the job's own sizes, `streams` streams back to back, timed in C
     (set_copy_bandwidth): H2D alone, D2H alone, and H2D + D2H together (total bytes both ways)."""
@@ -475,6 +538,10 @@ def run_set(args, d: Dist):
         ms_map, st_map = timed(S, ctxm, w.descs_host, nj, args, d)
         S.set_destroy(ctxm)
 
+    dd_arm = None
+    if not _profiler_attached() and not args.no_dd:
+        dd_arm = device_dispatch_arm(S, w, args.lanes, dev_index, args, d)
+
     k_mean_us, k_med_us = kernel_time(S, w)
     rates = copy_rates(S, JOB_IN, JOB_OUT, args.streams)
     world = d.world
@@ -526,6 +593,7 @@ def run_set(args, d: Dist):
             "p99_us": st_map["p99_us"],
             "note": "SET_IO_MAPPED: the same pinned host buffers, read and written by the kernels over "
                     "NVLink-C2C; the job graphs have no copy nodes"},
+        "device_dispatch": dd_arm,
         "gpu_launches": args.steps * nj * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
@@ -791,6 +859,38 @@ def run_bind_study(args, d: Dist):
                                       "mean_queue_us": st["mean_queue_us"]}), flush=True)
 
 
+def run_dd_study(args, d: Dist):
+    """Device-dispatch lanes (set_dd) against the host-dispatched executor on the scan jobs: one JSON
+    line per (io, lanes) and one for the executor's HBM-resident arm."""
+    import paper_2606_05495_gb300 as S
+    t = _torch()
+    t.cuda.set_device(d.local)
+    w = Workload(S, shard(args.jobs, d.rank), d.local)
+    nj = len(w.ids)
+    cfg = dict(num_streams=args.streams, num_workers=args.workers, ring_depth=args.ring, cb_mode=args.cb_mode,
+               cb_every=args.cb_every, device=d.local, io_mode=S.SET_IO_DEVICE,
+               slot_bytes=S.set_job_slot_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)))
+    ctx = S.create(S.default_config(**cfg))
+    ms, st = timed(S, ctx, w.descs_dev, nj, args, d)
+    S.set_destroy(ctx)
+    if d.rank == 0:
+        print(json.dumps({"workload": "dd-study", "arm": "executor", "io": "device", "streams": args.streams,
+                          "workers": args.workers, "jobs_per_s": nj * d.world / (ms * 1e-3),
+                          "p99_us": st["p99_us"], "mean_launch_us": st["mean_launch_us"]}), flush=True)
+    for lanes in (4, 8, 16, 32, 64):
+        dd = S.dd_create(S.dd_default_config(num_lanes=lanes, device=d.local))
+        try:
+            for io, descs in (("device", w.descs_dev), ("host-mapped", w.descs_host)):
+                ms, st, launches = timed_dd(S, dd, descs, nj, args, d)
+                if d.rank == 0:
+                    print(json.dumps({"workload": "dd-study", "arm": "set_dd", "io": io, "lanes": lanes,
+                                      "jobs_per_s": nj * d.world / (ms * 1e-3), "p50_us": st["p50_us"],
+                                      "p99_us": st["p99_us"], "submit_us": st["mean_launch_us"],
+                                      "ring_waits": st["mem_waits"], "graph_launches": launches}), flush=True)
+        finally:
+            S.set_dd_destroy(dd)
+
+
 def run_workload(args, d: Dist):
     """One JSON line per workload: SET forms against the batch-synchronous graph baseline."""
     import paper_2606_05495_gb300 as S
@@ -989,6 +1089,8 @@ def main():
             run_bind_study(args, d)
         elif args.workload == "copy-rates":
             run_copy_rates(args, d)
+        elif args.workload == "dd-study":
+            run_dd_study(args, d)
         elif args.workload != "scan":
             run_workload(args, d)
         else:

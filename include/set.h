@@ -391,6 +391,69 @@ set_status set_autotune(set_ctx* ctx, uint32_t type, const set_job_desc* sample,
 set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uint64_t* arrival_ns, size_t n,
                      set_stats_t* out);
 
+/* ---- device-side dispatch (a variant of the executor; set_dd_*) ----
+ *
+ * Moves dispatch and stage chaining onto the GPU.  Each lane is one stream running one graph:
+ *   WHILE (loop) { fetch kernel -> SWITCH (kind) { blur kernel | scan kernel } }.
+ * set_dd_submit writes the job's descriptor (its kernel argument struct, planned on the host)
+ * into a ring of the chosen lane in page-locked host memory.  The fetch kernel of each loop
+ * iteration retires the job the previous iteration ran (a completion word and a counter written
+ * to host memory, which a thread of the context reads to complete the job), waits a bounded time
+ * for the next descriptor, copies its arguments into the lane's device memory and selects the
+ * SWITCH body.  Per job the host writes one descriptor: no graph update, no graph launch and no
+ * host callback.  A lane whose fetch sees no descriptor for idle_us ends its loop; the host
+ * relaunches the lane's graph when work arrives.  The paper's executor (set_create) keeps the host
+ * in the loop; this variant measures the device-side alternative.
+ *
+ * Limits: SET_JOB_BLUR_HIST and SET_JOB_SAXPY_SCAN_MAX only (kernels whose graph node can keep
+ * one launch shape for every job of the lane: the scan node's grid covers scan_max_n, the blur
+ * node's shared memory blur_max_w).  in / out must be addresses the GPU can use as they are:
+ * device memory of the context's GPU, or page-locked host memory mapped at the same address
+ * (checked at submit, SET_EINVAL otherwise); the kernels read and write them in place.  The
+ * trailer's slot_gen holds the index of the lane that ran the job.  Thread safety as set_ctx. */
+typedef struct set_dd set_dd; /* opaque: lanes, their graphs, rings and completion thread */
+
+typedef struct {
+  int num_lanes;         /* streams, one looping graph each (default 16) */
+  int ring_depth;        /* descriptors per lane, rounded up to a power of two (default 64) */
+  int device;            /* CUDA device ordinal (default 0) */
+  uint32_t scan_max_n;   /* largest scan n accepted (default 65536, at most the scan limit 2^26) */
+  uint32_t blur_max_w;   /* largest blur width accepted (default 256, at most the blur limit) */
+  int idle_us;           /* a lane's loop ends after this long without a descriptor (default 2000) */
+  int spin_us;           /* the completion thread spins this long after progress before it
+                            sleeps in 5 us steps (default 50) */
+  int drain_timeout_ms;  /* set_dd_destroy waits at most this long for submitted jobs (default 30000) */
+} set_dd_config;
+
+void set_dd_config_default(set_dd_config* cfg);
+
+/* Allocates the rings (host) and lane state (device), builds and uploads each lane's graph and
+ * starts the completion thread.  Lanes start idle: the first descriptor launches the loop. */
+set_status set_dd_create(const set_dd_config* cfg, set_dd** out);
+
+/* Validates the descriptor, plans the job's kernel arguments, waits for a free entry in the
+ * ring of the lane with the fewest jobs in flight (lowest index on ties) unless SET_F_NONBLOCK
+ * (SET_EAGAIN), publishes the entry and relaunches the lane's graph if its loop has ended. */
+set_status set_dd_submit(set_dd* dd, const set_job_desc* job, uint64_t* job_id);
+set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, uint64_t* first_id, size_t* n_done);
+
+/* As set_wait_all. */
+set_status set_dd_wait_all(set_dd* dd, int64_t timeout_us);
+
+/* Counters and latencies as set_stats (steals, updates, mem_waits, arena and stamp fields 0;
+ * mean_update_us 0; mean_launch_us = host time of set_dd_submit per job; mean_queue_us and
+ * mean_service_us NaN).  *graph_launches (may be NULL) gets the lane graph launches so far. */
+set_status set_dd_stats(set_dd* dd, set_stats_t* out, uint64_t* graph_launches);
+set_status set_dd_reset_stats(set_dd* dd);
+
+/* Waits (drain_timeout_ms) for submitted jobs, tells every lane to end its loop, waits for the
+ * lanes' streams, joins the completion thread and frees everything.  If a lane does not end,
+ * its memory is left allocated (a kernel may still use it) and SET_ETIMEDOUT is returned. */
+set_status set_dd_destroy(set_dd* dd);
+
+/* Last error text of this object (or of the calling thread's last set_dd_create when NULL). */
+const char* set_dd_last_error(set_dd* dd);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,11 @@ class set_tune_result(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class set_dd_config(ctypes.Structure):
+    _fields_ = [("num_lanes", c_int), ("ring_depth", c_int), ("device", c_int), ("scan_max_n", c_uint32),
+                ("blur_max_w", c_uint32), ("idle_us", c_int), ("spin_us", c_int), ("drain_timeout_ms", c_int)]
+
+
 class SetError(RuntimeError):
     def __init__(self, status: int, where: str, text: str = ""):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {text}".strip())
@@ -123,6 +128,15 @@ _SIGS = {
     "set_autotune": ([c_void_p, c_uint32, POINTER(set_job_desc), c_size_t, POINTER(set_tune_result)], c_int),
     "set_serve": ([c_void_p, c_int, POINTER(set_job_desc), POINTER(c_uint64), c_size_t, POINTER(set_stats_t)], c_int),
     "set_trace_stop": ([POINTER(set_trace_summary)], c_int),
+    "set_dd_config_default": ([POINTER(set_dd_config)], None),
+    "set_dd_create": ([POINTER(set_dd_config), POINTER(c_void_p)], c_int),
+    "set_dd_submit": ([c_void_p, POINTER(set_job_desc), POINTER(c_uint64)], c_int),
+    "set_dd_submit_many": ([c_void_p, POINTER(set_job_desc), c_size_t, POINTER(c_uint64), POINTER(c_size_t)], c_int),
+    "set_dd_wait_all": ([c_void_p, c_int64], c_int),
+    "set_dd_stats": ([c_void_p, POINTER(set_stats_t), POINTER(c_uint64)], c_int),
+    "set_dd_reset_stats": ([c_void_p], c_int),
+    "set_dd_destroy": ([c_void_p], c_int),
+    "set_dd_last_error": ([c_void_p], c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -179,3 +193,25 @@ def default_config(**kw) -> set_config:
     for k, v in kw.items():
         setattr(c, k, v)
     return c
+
+
+def dd_default_config(**kw) -> set_dd_config:
+    c = set_dd_config()
+    set_dd_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def dd_check(status: int, where: str, dd=None) -> None:
+    """check() for the device-dispatch object (set_dd_last_error's text)."""
+    if status != SET_OK:
+        txt = set_dd_last_error(dd)
+        raise SetError(status, where, txt.decode() if txt else "")
+
+
+def dd_create(cfg: set_dd_config) -> c_void_p:
+    """set_dd_create that raises on failure; returns the handle."""
+    dd = c_void_p()
+    dd_check(set_dd_create(ctypes.byref(cfg), ctypes.byref(dd)), "set_dd_create")
+    return dd

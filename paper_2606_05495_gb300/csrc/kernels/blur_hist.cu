@@ -34,8 +34,9 @@ struct BlurHistArgs {
   uint32_t slot_gen, npad;
 };
 
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
-    blur_hist_kernel(const BlurHistArgs a) {
+// The whole kernel body: shared by the kernel that takes its arguments by value and the
+// device-dispatch lane kernel that reads them from device memory.
+__device__ __forceinline__ void blur_hist_body(const BlurHistArgs& a) {
   extern __shared__ __align__(16) uint8_t tile[];  // (kChunkRows + 2) rows x pitch
   __shared__ uint32_t whist[kWarps][256];
   __shared__ uint32_t chist[256];
@@ -130,6 +131,20 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
   stamp_exit(a.stamp);
 }
 
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
+    blur_hist_kernel(const __grid_constant__ BlurHistArgs a) {
+  blur_hist_body(a);
+}
+
+// Device-dispatch lane kernel: arguments of the job in flight in device memory (written by the
+// lane's fetch kernel); the node's dynamic shared memory covers the lane's widest image.
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
+    blur_hist_lane_kernel(const BlurHistArgs* __restrict__ pa) {
+  blur_hist_body(*pa);
+}
+
+inline unsigned blur_smem(uint32_t W) { return (unsigned)((kChunkRows + 2) * ((W + 15) & ~15u)); }
+
 inline size_t blur_img_bytes(const uint32_t d[4]) { return (size_t)d[0] * d[1]; }
 
 }  // namespace
@@ -152,7 +167,7 @@ bool plan_blur_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, i
   k.func = reinterpret_cast<const void*>(&blur_hist_kernel);
   k.grid = dim3(kCluster);
   k.block = dim3(kThreads);
-  k.smem = (unsigned)((kChunkRows + 2) * ((in.dims[0] + 15) & ~15u));
+  k.smem = blur_smem(in.dims[0]);
   k.deps = 0;
   set_args(k, a);
   *nk = 1;
@@ -160,8 +175,14 @@ bool plan_blur_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, i
 }
 
 cudaError_t blur_hist_init() {
-  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&blur_hist_kernel),
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (kChunkRows + 2) * kMaxW);
+  for (const void* f : {reinterpret_cast<const void*>(&blur_hist_kernel), reinterpret_cast<const void*>(&blur_hist_lane_kernel)}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (kChunkRows + 2) * kMaxW);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
+
+const void* blur_lane_func() { return reinterpret_cast<const void*>(&blur_hist_lane_kernel); }
+unsigned blur_lane_smem(uint32_t max_w) { return blur_smem(max_w); }
 
 }  // namespace setk

@@ -1,0 +1,71 @@
+// dev_dispatch.h -- memory layout shared by the host side of the device-dispatch lanes and their
+// fetch kernel.
+//
+// A lane is one stream running one graph: WHILE { fetch -> SWITCH(kind) { blur | scan } }.
+// The host writes job descriptors into the lane's ring (page-locked host memory the GPU reads
+// over the host link); the fetch kernel of each iteration retires the job the previous iteration
+// ran (completion word and counter into host memory), waits a bounded time for the next
+// descriptor, copies its kernel arguments into the lane's device block and selects the kind for
+// the SWITCH node.  No descriptor within the idle limit: it ends the loop and counts an exit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "set.h"
+
+namespace setk {
+
+constexpr uint32_t kDdKindBlur = 0, kDdKindScan = 1, kDdKinds = 2;
+constexpr uint32_t kDdKindNone = 7;  // >= the SWITCH node's body count: no body runs
+constexpr size_t kDdArgBytes = 192;
+
+// One ring entry: 32 8-byte words, read by the fetch kernel's warp with one word per thread.
+// The host fills words 1..31, then stores seq (word 0) with release order.
+struct alignas(64) DdEntry {
+  uint64_t seq;           // position in the lane's sequence + 1 once the entry is complete
+  uint32_t kind;          // kDdKind*
+  uint32_t args_size;     // bytes of args used
+  uint64_t job_id;        // echoed in the trailer the job's kernel writes
+  set_trailer* trailer;   // the job's trailer (device-usable address)
+  uint64_t pad[4];
+  unsigned char args[kDdArgBytes];  // the stage kernel's argument struct
+};
+static_assert(sizeof(DdEntry) == 256, "one entry = 32 words of 8 bytes");
+
+// Per-lane control words in host memory (one 64-byte line each).
+struct alignas(64) DdCtl {
+  uint64_t done;   // device -> host: jobs of this lane retired (release order)
+  uint32_t exits;  // device -> host: times the lane's loop has ended
+  uint32_t stop;   // host -> device: end the loop at the next fetch
+  uint64_t pad[6];
+};
+static_assert(sizeof(DdCtl) == 64, "one line per lane");
+
+// Per-lane state in device memory, kept across launches of the lane's graph.
+struct alignas(64) DdLaneDev {
+  uint64_t head;             // descriptors fetched so far
+  uint64_t cur_seq;          // head value of the job in flight (0: none to retire)
+  uint64_t cur_job;          // its job id
+  set_trailer* cur_trailer;  // its trailer
+  uint32_t exits;            // loop exits so far (mirrors DdCtl::exits)
+  uint32_t pad0;
+  uint64_t pad1[3];
+  alignas(64) unsigned char args[kDdKinds][kDdArgBytes];  // argument struct of each kind's node
+};
+
+struct DdFetchArgs {
+  DdLaneDev* lane;
+  const DdEntry* ring;  // device-usable address of the lane's ring
+  DdCtl* ctl;           // device-usable address of the lane's control line
+  uint32_t* cmpl;       // device-usable address of the lane's completion words (one per ring entry)
+  uint32_t depth;       // ring entries (power of two)
+  uint32_t pad;
+  uint64_t idle_ns;     // end the loop after this long without a descriptor
+  cudaGraphConditionalHandle loop;  // WHILE node condition
+  cudaGraphConditionalHandle kind;  // SWITCH node selector
+};
+
+}  // namespace setk

@@ -75,7 +75,9 @@ __device__ __forceinline__ uint64_t max_word(uint32_t epoch, float m) {
   return ((uint64_t)(epoch | 0x80000000u) << 32) | (uint64_t)__float_as_uint(m);
 }
 
-__global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs p) {
+// One tile of the job (the whole kernel body): shared by the kernel that takes its arguments by
+// value and the device-dispatch lane kernel that reads them from device memory.
+__device__ __forceinline__ void scan_tile(const ScanArgs& p, const uint32_t tile) {
   __shared__ float s_wsum[kWarps], s_wexcl[kWarps], s_wmax[kWarps];
   __shared__ float s_prefix;
   ScanHdr* hdr = reinterpret_cast<ScanHdr*>(p.scratch);
@@ -87,7 +89,6 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   // has started.  The epoch load is issued first and only consumed by the look-back, so its
   // latency overlaps the data loads.
   stamp_entry(p.stamp);
-  const uint32_t tile = blockIdx.x;
   if (tile == p.skip_tile) {  // test hook: the look-back of the next tile and the max gather time out
     stamp_exit(p.stamp);
     return;
@@ -275,9 +276,24 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const ScanArgs
   stamp_exit(p.stamp);
 }
 
+__global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_constant__ ScanArgs p) {
+  scan_tile(p, blockIdx.x);
+}
+
+// Device-dispatch lane kernel: the graph node's grid is fixed (the lane's largest job); the
+// arguments of the job in flight sit in device memory, written by the lane's fetch kernel, and
+// blocks past the job's tile count leave at once.
+__global__ void __launch_bounds__(kThreads) saxpy_scan_max_lane_kernel(const ScanArgs* __restrict__ pa) {
+  if (blockIdx.x >= pa->T) return;
+  scan_tile(*pa, blockIdx.x);
+}
+
 inline uint32_t num_tiles(uint32_t n) { return (n + kTile - 1) / kTile; }
 
 }  // namespace
+
+const void* scan_lane_func() { return reinterpret_cast<const void*>(&saxpy_scan_max_lane_kernel); }
+uint32_t scan_lane_grid(uint32_t max_n) { return num_tiles(max_n); }
 
 bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk) {
   const uint32_t n = in.dims[0];

@@ -106,6 +106,15 @@ bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
 // the slot at slot_base (plant: the SET_F_TEST_GUARD hook).
 void plan_guards(uint8_t* slot_base, const JobLayout& L, bool plant, KernelLaunch* arm, KernelLaunch* check);
 
+// Device-dispatch lane kernels (one argument: a pointer to the job's argument struct in device
+// memory) and their fixed launch shapes: the scan node's grid for the lane's largest n, the blur
+// node's dynamic shared memory for its widest image.
+const void* scan_lane_func();
+uint32_t scan_lane_grid(uint32_t max_n);
+const void* blur_lane_func();
+unsigned blur_lane_smem(uint32_t max_w);
+const void* dd_fetch_func();
+
 // One-time function attributes (dynamic shared memory limits, cluster sizes).
 cudaError_t kernels_init();
 cudaError_t blur_hist_init();

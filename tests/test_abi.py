@@ -37,6 +37,7 @@ STRUCTS = {
     "set_trailer": S.set_trailer,
     "set_trace_summary": S.set_trace_summary,
     "set_tune_result": S.set_tune_result,
+    "set_dd_config": S.set_dd_config,
 }
 
 
@@ -96,3 +97,19 @@ def test_create_without_gpu_fails_cleanly():
     assert S.set_create(2, 2, 1 << 20, ctypes.byref(ctx)) == S.SET_ECUDA
     assert S.set_last_error(None)
     assert S.set_submit(None, None, None) == S.SET_EINVAL
+
+
+def test_dd_config_defaults_and_validation_without_gpu():
+    c = S.dd_default_config()
+    assert (c.num_lanes, c.ring_depth, c.scan_max_n, c.blur_max_w, c.idle_us) == (16, 64, 65536, 256, 2000)
+    dd = ctypes.c_void_p()
+    # configuration is checked before any CUDA call
+    for bad in (dict(num_lanes=0), dict(ring_depth=0), dict(scan_max_n=0), dict(scan_max_n=(1 << 26) + 1),
+                dict(blur_max_w=2049), dict(idle_us=0)):
+        assert S.set_dd_create(ctypes.byref(S.dd_default_config(**bad)), ctypes.byref(dd)) == S.SET_EINVAL
+        assert not dd.value and S.set_dd_last_error(None)
+    assert S.set_dd_submit(None, None, None) == S.SET_EINVAL
+    assert S.set_dd_wait_all(None, 0) == S.SET_EINVAL
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert S.set_dd_create(ctypes.byref(c), ctypes.byref(dd)) == S.SET_ECUDA and not dd.value

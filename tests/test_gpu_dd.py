@@ -1,0 +1,197 @@
+"""GPU parity of the device-dispatch lanes (set_dd_*): jobs fetched and run by looping lane graphs."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+from gpu_util import S, blur_job, check_blur, check_scan, scan_job
+
+pytestmark = pytest.mark.gpu
+
+
+def run_dd(jobs, timeout_s=120, **cfg):
+    """Submits every job through set_dd_submit_many, waits, destroys; returns (stats, launches)."""
+    s = S()
+    dd = s.dd_create(s.dd_default_config(**cfg))
+    try:
+        arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+        first = ctypes.c_uint64()
+        s.dd_check(s.set_dd_submit_many(dd, arr, len(jobs), ctypes.byref(first), None), "set_dd_submit_many", dd)
+        s.dd_check(s.set_dd_wait_all(dd, int(timeout_s * 1e6)), "set_dd_wait_all", dd)
+        for k, j in enumerate(jobs):
+            j.id = first.value + k
+        st, launches = s.set_stats_t(), ctypes.c_uint64()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), ctypes.byref(launches)), "set_dd_stats", dd)
+        return st.as_dict(), launches.value
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+
+
+def check_dd_trailers(jobs, lanes):
+    s = S()
+    for j in jobs:
+        jid, gen, word = j.trailer()
+        assert jid == j.id, (jid, j.id)
+        assert gen < lanes, gen  # slot_gen carries the lane index
+        assert word == (s.SET_TRAILER_MAGIC << 16), hex(word)
+        assert j.status.value == s.SET_OK, j.status.value
+
+
+def test_single_jobs_one_lane():
+    jobs = [scan_job(1, n=65536, device=True), blur_job(2, device=True)]
+    st, launches = run_dd(jobs, num_lanes=1)
+    assert st["completed"] == 2 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    assert launches >= 1
+    check_scan(jobs[0])
+    check_blur(jobs[1])
+    check_dd_trailers(jobs, 1)
+
+
+def test_scan_jobs_hbm_resident_16_lanes():
+    jobs = [scan_job(k, device=True) for k in range(512)]
+    st, launches = run_dd(jobs, num_lanes=16)
+    assert st["completed"] == 512 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    assert launches >= 1
+    for j in jobs:
+        check_scan(j)
+    check_dd_trailers(jobs, 16)
+
+
+def test_blur_jobs_hbm_resident():
+    jobs = [blur_job(k, device=True) for k in range(64)]
+    st, _ = run_dd(jobs, num_lanes=2)
+    assert st["completed"] == 64 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        check_blur(j)
+    check_dd_trailers(jobs, 2)
+
+
+def test_mixed_kinds_and_ragged_sizes_share_lanes():
+    # one lane graph runs both kinds (SWITCH) and sizes below its fixed launch shape (spare scan
+    # blocks leave at once; the blur node's shared memory covers the widest image)
+    jobs = []
+    for k, n in enumerate([1, 2, 5, 4095, 4096, 4097, 30001, 65535, 65536, 7, 100, 8192]):
+        jobs.append(scan_job(300 + k, n=n, device=True))
+    for k, (W, H) in enumerate([(1, 1), (1, 9), (9, 1), (16, 16), (17, 3), (255, 257), (256, 1000), (33, 7)]):
+        jobs.append(blur_job(400 + k, W=W, H=H, device=True))
+    order = np.random.default_rng(5).permutation(len(jobs))
+    jobs = [jobs[i] for i in order]
+    st, _ = run_dd(jobs, num_lanes=3, ring_depth=4)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+    check_dd_trailers(jobs, 3)
+
+
+def test_mapped_host_buffers():
+    # page-locked host in/out: the lane kernels read and write them in place over the host link
+    jobs = [scan_job(600 + k, n=20000 + 3 * k) for k in range(24)] + [blur_job(700 + k) for k in range(8)]
+    st, _ = run_dd(jobs, num_lanes=4)
+    assert st["completed"] == 32 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+    check_dd_trailers(jobs, 4)
+
+
+def test_idle_lanes_end_their_loop_and_are_relaunched():
+    s = S()
+    dd = s.dd_create(s.dd_default_config(num_lanes=2, idle_us=200))
+    try:
+        jobs = []
+        launches = ctypes.c_uint64()
+        st = s.set_stats_t()
+        for wave in range(3):
+            batch = [scan_job(800 + 10 * wave + k, n=10000 + k, device=True) for k in range(6)]
+            arr = (s.set_job_desc * len(batch))(*[j.desc for j in batch])
+            first = ctypes.c_uint64()
+            s.dd_check(s.set_dd_submit_many(dd, arr, len(batch), ctypes.byref(first), None), "submit", dd)
+            s.dd_check(s.set_dd_wait_all(dd, 60_000_000), "wait", dd)
+            for k, j in enumerate(batch):
+                j.id = first.value + k
+            jobs += batch
+            time.sleep(0.05)  # far beyond idle_us: both loops end
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), ctypes.byref(launches)), "stats", dd)
+        assert st.completed == 18 and st.failed == 0
+        assert launches.value >= 6, launches.value  # each wave relaunched both lanes
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+    for j in jobs:
+        check_scan(j)
+    check_dd_trailers(jobs, 2)
+
+
+def test_bounded_device_wait_reports_and_lane_continues():
+    s = S()
+    jobs = [scan_job(900 + k, n=65536, device=True) for k in range(5)]
+    jobs[2].desc.flags = s.SET_F_TEST_STALL
+    st, _ = run_dd(jobs, num_lanes=1)
+    assert st["completed"] == 5 and st["failed"] == 1 and st["canary_errors"] == 0, st
+    assert jobs[2].status.value == s.SET_EDEVICE
+    _, _, word = jobs[2].trailer()
+    assert word == (s.SET_TRAILER_MAGIC << 16) | s.SET_DEVERR_WAIT, hex(word)
+    for k in (0, 1, 3, 4):
+        assert jobs[k].status.value == s.SET_OK
+        check_scan(jobs[k])
+
+
+def test_full_ring_nonblocking_submit_returns_eagain():
+    s = S()
+    dd = s.dd_create(s.dd_default_config(num_lanes=1, ring_depth=1))
+    try:
+        slow = scan_job(950, n=65536, device=True)
+        slow.desc.flags = s.SET_F_TEST_STALL  # holds the lane's only entry for >= 0.1 s
+        s.dd_check(s.set_dd_submit(dd, ctypes.byref(slow.desc), None), "submit", dd)
+        nb = scan_job(951, n=4096, device=True)
+        nb.desc.flags = s.SET_F_NONBLOCK
+        assert s.set_dd_submit(dd, ctypes.byref(nb.desc), None) == s.SET_EAGAIN
+        nb.desc.flags = 0
+        jid = ctypes.c_uint64()
+        s.dd_check(s.set_dd_submit(dd, ctypes.byref(nb.desc), ctypes.byref(jid)), "blocking submit", dd)
+        nb.id = jid.value
+        s.dd_check(s.set_dd_wait_all(dd, 60_000_000), "wait", dd)
+        st = s.set_stats_t()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
+        assert st.mem_waits >= 1 and st.completed == 2 and st.failed == 1
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+    check_scan(nb)
+    check_dd_trailers([nb], 1)
+
+
+def test_rejects_what_a_lane_cannot_run():
+    s, t = S(), __import__("torch")
+    from gpu_util import img_job
+    dd = s.dd_create(s.dd_default_config(num_lanes=1, scan_max_n=8192, blur_max_w=64))
+    try:
+        big = scan_job(960, n=8193, device=True)
+        wide = blur_job(961, W=65, H=4, device=True)
+        img = img_job(962, dims=(32, 32), device=True)
+        for j in (big, wide, img):
+            assert s.set_dd_submit(dd, ctypes.byref(j.desc), None) == s.SET_EINVAL
+        pageable_in = np.zeros(8 * 100, np.uint8)
+        out = t.zeros(s.set_job_out_bytes(2, s.dims4(100)), dtype=t.uint8, device="cuda")
+        d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (100,), pageable_in.ctypes.data, out.data_ptr())
+        assert s.set_dd_submit(dd, ctypes.byref(d), None) == s.SET_EINVAL
+        assert b"page-locked" in s.set_dd_last_error(dd)
+        st = s.set_stats_t()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
+        assert st.submitted == 0
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+
+
+def test_destroy_with_jobs_in_flight_completes_them():
+    s = S()
+    jobs = [scan_job(1000 + k, n=30000 + 11 * k, device=True) for k in range(200)]
+    dd = s.dd_create(s.dd_default_config(num_lanes=4, ring_depth=8))
+    arr = (s.set_job_desc * len(jobs))(*[j.desc for j in jobs])
+    first = ctypes.c_uint64()
+    try:
+        s.dd_check(s.set_dd_submit_many(dd, arr, len(jobs), ctypes.byref(first), None), "submit", dd)
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+    for k, j in enumerate(jobs):
+        j.id = first.value + k
+        check_scan(j)
+    check_dd_trailers(jobs, 4)
