@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
     p.add_argument("--lanes", type=int, default=16, help="device-dispatch arm (set_dd): lanes")
-    p.add_argument("--no-dd", action="store_true", help="skip the device-dispatch arm")
+    p.add_argument("--dd-arm", action="store_true", help="add the device-dispatch arm (set_dd) to the scan line")
     p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates",
                                           "dd-study"],
                    default="scan",
@@ -384,14 +384,12 @@ def timed_dd(S, dd, descs, n, args, d: Dist):
 
 
 def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: Dist):
-    """The same scan jobs through set_dd (lane graphs that fetch and run jobs on the device):
-    HBM-resident buffers, then the pinned host buffers read and written in place, then one
-    CUPTI-traced HBM step for the device-timeline gaps."""
+    """The same HBM-resident scan jobs through set_dd (lane graphs that fetch and run jobs on the
+    device), then one CUPTI-traced step for the device-timeline gaps."""
     nj = len(w.ids)
     dd = S.dd_create(S.dd_default_config(num_lanes=lanes, device=dev_index))
     try:
         ms_d, st_d, launches = timed_dd(S, dd, w.descs_dev, nj, args, d)
-        ms_h, st_h, _ = timed_dd(S, dd, w.descs_host, nj, args, d)
         gap = None
         tr = S.set_trace_summary()
         if S.set_trace_start() == S.SET_OK:
@@ -405,10 +403,7 @@ def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: D
     return {
         "value": world * nj / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "lanes": lanes,
         "p50_us": st_d["p50_us"], "p99_us": st_d["p99_us"], "submit_us": st_d["mean_launch_us"],
-        "graph_launches": launches,
-        "e2e_mapped": {"value": world * nj / (ms_h * 1e-3), "unit": UNIT, "ms_per_step": ms_h,
-                       "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
-                       "p50_us": st_h["p50_us"], "p99_us": st_h["p99_us"]},
+        "graph_launches": launches, "failed": st_d["failed"], "canary_errors": st_d["canary_errors"],
         "trace": gap,
         "note": "set_dd: per lane one graph WHILE {fetch -> SWITCH {scan}} looping on the device; the host "
                 "writes one descriptor per job (no graph update, launch or callback per job)",
@@ -539,7 +534,7 @@ def run_set(args, d: Dist):
         S.set_destroy(ctxm)
 
     dd_arm = None
-    if not _profiler_attached() and not args.no_dd:
+    if not _profiler_attached() and args.dd_arm:
         dd_arm = device_dispatch_arm(S, w, args.lanes, dev_index, args, d)
 
     k_mean_us, k_med_us = kernel_time(S, w)
@@ -860,35 +855,30 @@ def run_bind_study(args, d: Dist):
 
 
 def run_dd_study(args, d: Dist):
-    """Device-dispatch lanes (set_dd) against the host-dispatched executor on the scan jobs: one JSON
-    line per (io, lanes) and one for the executor's HBM-resident arm."""
+    """Device-dispatch lanes (set_dd) against the host-dispatched executor on the HBM-resident scan
+    jobs: one JSON line per lane count and one for the executor."""
     import paper_2606_05495_gb300 as S
     t = _torch()
     t.cuda.set_device(d.local)
     w = Workload(S, shard(args.jobs, d.rank), d.local)
     nj = len(w.ids)
-    cfg = dict(num_streams=args.streams, num_workers=args.workers, ring_depth=args.ring, cb_mode=args.cb_mode,
-               cb_every=args.cb_every, device=d.local, io_mode=S.SET_IO_DEVICE,
-               slot_bytes=S.set_job_slot_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)))
-    ctx = S.create(S.default_config(**cfg))
-    ms, st = timed(S, ctx, w.descs_dev, nj, args, d)
-    S.set_destroy(ctx)
-    if d.rank == 0:
-        print(json.dumps({"workload": "dd-study", "arm": "executor", "io": "device", "streams": args.streams,
-                          "workers": args.workers, "jobs_per_s": nj * d.world / (ms * 1e-3),
-                          "p99_us": st["p99_us"], "mean_launch_us": st["mean_launch_us"]}), flush=True)
+    for streams in (8, 16):
+        cfg = dict(num_streams=streams, num_workers=args.workers, ring_depth=args.ring, cb_mode=args.cb_mode,
+                   cb_every=args.cb_every, device=d.local, io_mode=S.SET_IO_DEVICE,
+                   slot_bytes=S.set_job_slot_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)))
+        ctx = S.create(S.default_config(**cfg))
+        ms, st = timed(S, ctx, w.descs_dev, nj, args, d)
+        S.set_destroy(ctx)
+        if d.rank == 0:
+            print(json.dumps({"workload": "dd-study", "arm": "executor", "io": "device", "streams": streams,
+                              "workers": args.workers, "jobs_per_s": nj * d.world / (ms * 1e-3),
+                              "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                              "mean_launch_us": st["mean_launch_us"]}), flush=True)
     for lanes in (4, 8, 16, 32, 64):
-        dd = S.dd_create(S.dd_default_config(num_lanes=lanes, device=d.local))
-        try:
-            for io, descs in (("device", w.descs_dev), ("host-mapped", w.descs_host)):
-                ms, st, launches = timed_dd(S, dd, descs, nj, args, d)
-                if d.rank == 0:
-                    print(json.dumps({"workload": "dd-study", "arm": "set_dd", "io": io, "lanes": lanes,
-                                      "jobs_per_s": nj * d.world / (ms * 1e-3), "p50_us": st["p50_us"],
-                                      "p99_us": st["p99_us"], "submit_us": st["mean_launch_us"],
-                                      "ring_waits": st["mem_waits"], "graph_launches": launches}), flush=True)
-        finally:
-            S.set_dd_destroy(dd)
+        arm = device_dispatch_arm(S, w, lanes, d.local, args, d)
+        if d.rank == 0:
+            print(json.dumps({"workload": "dd-study", "arm": "set_dd", "io": "device", "jobs_per_s": arm["value"],
+                              **{k: v for k, v in arm.items() if k not in ("value", "unit", "note")}}), flush=True)
 
 
 def run_workload(args, d: Dist):

@@ -407,9 +407,10 @@ set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uin
  *
  * Limits: SET_JOB_BLUR_HIST and SET_JOB_SAXPY_SCAN_MAX only (kernels whose graph node can keep
  * one launch shape for every job of the lane: the scan node's grid covers scan_max_n, the blur
- * node's shared memory blur_max_w).  in / out must be addresses the GPU can use as they are:
- * device memory of the context's GPU, or page-locked host memory mapped at the same address
- * (checked at submit, SET_EINVAL otherwise); the kernels read and write them in place.  The
+ * node's shared memory blur_max_w).  in / out must be 16-byte aligned device memory of the
+ * object's GPU (checked at submit, SET_EINVAL otherwise); the kernels read and write them in
+ * place.  Page-locked host buffers are refused: lane graphs whose kernels streamed them over the
+ * host link faulted the GPU in testing (cause not found), so that combination is closed.  The
  * trailer's slot_gen holds the index of the lane that ran the job.  Thread safety as set_ctx. */
 typedef struct set_dd set_dd; /* opaque: lanes, their graphs, rings and completion thread */
 

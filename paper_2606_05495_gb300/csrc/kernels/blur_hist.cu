@@ -140,6 +140,16 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
 // lane's fetch kernel); the node's dynamic shared memory covers the lane's widest image.
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
     blur_hist_lane_kernel(const BlurHistArgs* __restrict__ pa) {
+  // arguments that do not describe a job this node can run (an empty or too wide image for the
+  // node's shared memory, null or unaligned buffers) run nothing: every CTA of the cluster takes
+  // the same decision, the trailer stays unwritten and the fetch kernel reports it
+  uint32_t dsmem;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
+  const uint32_t W = pa->W, H = pa->H;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(pa->hist) | reinterpret_cast<uintptr_t>(pa->trailer);
+  if (W == 0 || H == 0 || W > (uint32_t)kMaxW || (uint64_t)(kChunkRows + 2) * ((W + 15) & ~15u) > dsmem || !pa->in ||
+      !pa->out || !pa->pad || (al & 7u) != 0)
+    return;
   blur_hist_body(*pa);
 }
 

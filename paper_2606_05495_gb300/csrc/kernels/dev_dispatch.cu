@@ -51,8 +51,11 @@ __global__ void __launch_bounds__(32) dd_fetch_kernel(const __grid_constant__ Dd
   if (lane == 0 && L->cur_seq != 0) {
     const uint64_t s = L->cur_seq;
     const volatile set_trailer* t = L->cur_trailer;
-    uint32_t word = t->word;
-    if (t->job_id != L->cur_job || (word >> 16) != SET_TRAILER_MAGIC) word = 0u;
+    uint32_t word = 0u;
+    if (t && (reinterpret_cast<uintptr_t>(t) & 7u) == 0) {
+      word = t->word;
+      if (t->job_id != L->cur_job || (word >> 16) != SET_TRAILER_MAGIC) word = 0u;
+    }
     st_relaxed_sys32(&a.cmpl[(s - 1) & (a.depth - 1)], word);
     st_release_sys(&a.ctl->done, s);
     L->cur_seq = 0;

@@ -284,7 +284,21 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_c
 // arguments of the job in flight sit in device memory, written by the lane's fetch kernel, and
 // blocks past the job's tile count leave at once.
 __global__ void __launch_bounds__(kThreads) saxpy_scan_max_lane_kernel(const ScanArgs* __restrict__ pa) {
-  if (blockIdx.x >= pa->T) return;
+  const uint32_t T = pa->T, n = pa->n;
+  if (blockIdx.x >= T) return;
+  // arguments that do not describe a job this node can run (a tile count beyond the grid, n out
+  // of the tiles' range, unaligned buffers) run nothing: the job's trailer stays unwritten and
+  // the fetch kernel reports it
+  // (x, z and the scratch start 16-byte aligned; y, S and m follow n floats later, and the
+  // kernel's 16-byte accesses to them are taken only when n is a multiple of 4; the trailer
+  // follows 8n + 16 bytes of output, so it is 8-byte aligned)
+  const uintptr_t al16 = reinterpret_cast<uintptr_t>(pa->x) | reinterpret_cast<uintptr_t>(pa->z) |
+                         reinterpret_cast<uintptr_t>(pa->scratch);
+  const uintptr_t al4 = reinterpret_cast<uintptr_t>(pa->y) | reinterpret_cast<uintptr_t>(pa->S) |
+                        reinterpret_cast<uintptr_t>(pa->m_out);
+  if (T > gridDim.x || n == 0 || n > T * kTile || n <= (T - 1) * kTile || (al16 & 15u) != 0 || (al4 & 3u) != 0 ||
+      (reinterpret_cast<uintptr_t>(pa->trailer) & 7u) != 0)
+    return;
   scan_tile(*pa, blockIdx.x);
 }
 

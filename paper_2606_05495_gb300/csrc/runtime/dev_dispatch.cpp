@@ -54,6 +54,7 @@ struct DdInfo {
 struct DdLane {
   std::mutex mu;  // writers of this lane's ring and graph launches
   cudaStream_t stream = nullptr;
+  cudaEvent_t ended = nullptr;  // recorded behind each launch of the lane's graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   setk::DdEntry* ring = nullptr;  // host view
@@ -70,16 +71,14 @@ struct DdLane {
 inline uint32_t load_acq32(const uint32_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 inline uint64_t load_acq64(const uint64_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 
-// Usable by the GPU at the same address: device (or managed) memory, or host memory mapped at
-// its own address.
-bool device_usable(const void* p) {
+// Device memory of `device` (the lanes' kernels read and write the job's buffers in place).
+bool device_memory(const void* p, int device) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 }  // namespace
@@ -208,6 +207,7 @@ set_status DevDispatch::init(const set_dd_config& cfg, std::string* err) {
 set_status DevDispatch::build_lane(uint32_t i, std::string* err) {
   DdLane& l = *lanes_[i];
   DD_CK(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
+  DD_CK(cudaEventCreateWithFlags(&l.ended, cudaEventDisableTiming));
   DD_CK(cudaGraphCreate(&l.graph, 0));
   cudaGraphConditionalHandle hloop = 0, hkind = 0;
   DD_CK(cudaGraphConditionalHandleCreate(&hloop, l.graph, 1u, cudaGraphCondAssignDefault));
@@ -219,7 +219,8 @@ set_status DevDispatch::build_lane(uint32_t i, std::string* err) {
   cudaGraphNode_t wn = nullptr;
   DD_CK(cudaGraphAddNode(&wn, l.graph, nullptr, nullptr, 0, &wp));
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  DD_CK(cudaGraphConditionalHandleCreate(&hkind, body, setk::kDdKindNone, cudaGraphCondAssignDefault));
+  // the fetch kernel sets the selector before the SWITCH node reads it in every iteration
+  DD_CK(cudaGraphConditionalHandleCreate(&hkind, body, setk::kDdKindNone, 0));
 
   // device-usable addresses of this lane's host-side structures
   void* ring_d = nullptr;
@@ -283,7 +284,8 @@ set_status DevDispatch::launch_locked(DdLane& l) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != cfg_.device) cudaSetDevice(cfg_.device);
-  const cudaError_t e = cudaGraphLaunch(l.exec, l.stream);
+  cudaError_t e = cudaGraphLaunch(l.exec, l.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(l.ended, l.stream);
   if (prev >= 0 && prev != cfg_.device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -293,11 +295,19 @@ set_status DevDispatch::launch_locked(DdLane& l) {
   return SET_OK;
 }
 
-// A lane needs a launch when descriptors wait and every loop launched so far has ended (its
-// fetch counted the exit before the loop stopped; a launch behind it on the stream is ordered).
+// A lane needs a launch when descriptors wait and every loop launched so far has ended: its
+// fetch counted the exit, and the graph has completed on the stream (the event behind the last
+// launch), so one launch of the lane's graph never waits behind another.
 bool DevDispatch::maybe_relaunch_locked(DdLane& l) {
   if (l.seq.load(std::memory_order_acquire) <= load_acq64(&l.ctl->done)) return false;
   if (load_acq32(&l.ctl->exits) != l.launches.load(std::memory_order_acquire)) return false;
+  const cudaError_t q = cudaEventQuery(l.ended);
+  if (q == cudaErrorNotReady) return false;
+  if (q != cudaSuccess) {
+    cudaGetLastError();
+    fail(SET_ECUDA, std::string("lane graph: ") + cudaGetErrorString(q));
+    return false;
+  }
   return launch_locked(l) == SET_OK;
 }
 
@@ -342,8 +352,12 @@ set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std:
     *why = "null in/out, or in_bytes/out_bytes do not match the job type's layout";
     return SET_EINVAL;
   }
-  if (!device_usable(d.in) || !device_usable(d.out)) {
-    *why = "set_dd: in/out must be device memory or page-locked host memory mapped at the same address";
+  if (!device_memory(d.in, cfg_.device) || !device_memory(d.out, cfg_.device)) {
+    *why = "set_dd: in/out must be device memory of the object's GPU";
+    return SET_EINVAL;
+  }
+  if (((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u) != 0) {
+    *why = "set_dd: in/out must be 16-byte aligned (the kernels use 16-byte accesses in place)";
     return SET_EINVAL;
   }
   return SET_OK;
@@ -586,6 +600,8 @@ void DevDispatch::release() {
   }
   if (leak_) return;
   for (auto& l : lanes_) {
+    if (l->ended) cudaEventDestroy(l->ended);
+    l->ended = nullptr;
     if (l->exec) cudaGraphExecDestroy(l->exec);
     if (l->graph) cudaGraphDestroy(l->graph);
     if (l->stream) cudaStreamDestroy(l->stream);

@@ -158,6 +158,11 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
     *why = "mapped I/O: in/out must be page-locked host memory (or device memory) the GPU can address";
     return SET_EINVAL;
   }
+  if ((io_maps_in(cfg_.io_mode) && (reinterpret_cast<uintptr_t>(d.in) & 15u)) ||
+      (io_maps_out(cfg_.io_mode) && (reinterpret_cast<uintptr_t>(d.out) & 15u))) {
+    *why = "mapped I/O: in/out must be 16-byte aligned (the kernels use 16-byte accesses in place)";
+    return SET_EINVAL;
+  }
   const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);
   if (use_arena_) {
     if (job_block_bytes(d) > arena_.max_block() || job_block_bytes(d) > cfg_.slot_bytes ||

@@ -84,14 +84,34 @@ def test_mixed_kinds_and_ragged_sizes_share_lanes():
     check_dd_trailers(jobs, 3)
 
 
-def test_mapped_host_buffers():
-    # page-locked host in/out: the lane kernels read and write them in place over the host link
-    jobs = [scan_job(600 + k, n=20000 + 3 * k) for k in range(24)] + [blur_job(700 + k) for k in range(8)]
-    st, _ = run_dd(jobs, num_lanes=4)
-    assert st["completed"] == 32 and st["failed"] == 0 and st["canary_errors"] == 0, st
-    for j in jobs:
-        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
-    check_dd_trailers(jobs, 4)
+def test_host_buffers_are_refused():
+    # page-locked host in/out are refused at submit (nothing runs on the GPU for them)
+    s = S()
+    dd = s.dd_create(s.dd_default_config(num_lanes=1))
+    try:
+        for j in (scan_job(600, n=4096), blur_job(601, W=32, H=32)):
+            assert s.set_dd_submit(dd, ctypes.byref(j.desc), None) == s.SET_EINVAL
+            assert b"device memory" in s.set_dd_last_error(dd)
+        st = s.set_stats_t()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
+        assert st.submitted == 0
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+
+
+def test_unaligned_device_buffers_are_refused():
+    s, t = S(), __import__("torch")
+    dd = s.dd_create(s.dd_default_config(num_lanes=1))
+    try:
+        n = 1000
+        buf_in = t.zeros(8 * n + 64, dtype=t.uint8, device="cuda")
+        buf_out = t.zeros(s.set_job_out_bytes(2, s.dims4(n)) + 64, dtype=t.uint8, device="cuda")
+        d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (n,), buf_in.data_ptr() + 4, buf_out.data_ptr())
+        assert s.set_dd_submit(dd, ctypes.byref(d), None) == s.SET_EINVAL
+        d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (n,), buf_in.data_ptr(), buf_out.data_ptr() + 8)
+        assert s.set_dd_submit(dd, ctypes.byref(d), None) == s.SET_EINVAL
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
 
 
 def test_idle_lanes_end_their_loop_and_are_relaunched():
@@ -173,7 +193,7 @@ def test_rejects_what_a_lane_cannot_run():
         out = t.zeros(s.set_job_out_bytes(2, s.dims4(100)), dtype=t.uint8, device="cuda")
         d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (100,), pageable_in.ctypes.data, out.data_ptr())
         assert s.set_dd_submit(dd, ctypes.byref(d), None) == s.SET_EINVAL
-        assert b"page-locked" in s.set_dd_last_error(dd)
+        assert b"device memory" in s.set_dd_last_error(dd)
         st = s.set_stats_t()
         s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
         assert st.submitted == 0
