@@ -355,25 +355,42 @@ def timed(S, ctx, descs, n, args, d: Dist, clocks: "Clocks | None" = None):
     return d.max(ms), st.as_dict()
 
 
-def run_step_dd(S, dd, descs, n):
-    done = ctypes.c_size_t()
-    S.dd_check(S.set_dd_submit_many(dd, descs, n, None, ctypes.byref(done)), "set_dd_submit_many", dd)
+_SUBMIT_POOLS = {}
+
+
+def run_step_dd(S, dd, descs, n, threads=1):
+    """One step through set_dd: submit every job (from `threads` host threads, each a contiguous
+    share of the descriptors), then wait for all."""
+    if threads <= 1:
+        done = ctypes.c_size_t()
+        S.dd_check(S.set_dd_submit_many(dd, descs, n, None, ctypes.byref(done)), "set_dd_submit_many", dd)
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        pool = _SUBMIT_POOLS.setdefault(threads, ThreadPoolExecutor(threads))
+        sz = ctypes.sizeof(S.set_job_desc)
+
+        def share(k):
+            a, b = k * n // threads, (k + 1) * n // threads
+            return S.set_dd_submit_many(dd, ctypes.byref(descs, a * sz), b - a, None, None)
+
+        for st in pool.map(share, range(threads)):
+            S.dd_check(st, "set_dd_submit_many", dd)
     S.dd_check(S.set_dd_wait_all(dd, 600_000_000), "set_dd_wait_all", dd)
 
 
-def timed_dd(S, dd, descs, n, args, d: Dist):
+def timed_dd(S, dd, descs, n, args, d: Dist, threads=1):
     """timed() for the device-dispatch lanes (set_dd): W warm-up steps, then K steps between CUDA
     events with a synchronize on both sides; returns (ms per step, stats, lane graph launches)."""
     t = _torch()
     for _ in range(args.warmup):
-        run_step_dd(S, dd, descs, n)
+        run_step_dd(S, dd, descs, n, threads)
     S.set_dd_reset_stats(dd)
     d.barrier()
     t.cuda.synchronize()
     e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        run_step_dd(S, dd, descs, n)
+        run_step_dd(S, dd, descs, n, threads)
     e1.record()
     t.cuda.synchronize()
     d.barrier()
@@ -383,19 +400,20 @@ def timed_dd(S, dd, descs, n, args, d: Dist):
     return d.max(ms), st.as_dict(), launches.value
 
 
-def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: Dist):
+def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: Dist, threads: int = 1):
     """The same HBM-resident scan jobs through set_dd (lane graphs that fetch and run jobs on the
     device).  No CUPTI trace: activity records of kernels launched by conditional graph nodes came
     back incomplete (12 of ~8,200 kernels in one run), so device-timeline gaps are not reported."""
     nj = len(w.ids)
     dd = S.dd_create(S.dd_default_config(num_lanes=lanes, device=dev_index))
     try:
-        ms_d, st_d, launches = timed_dd(S, dd, w.descs_dev, nj, args, d)
+        ms_d, st_d, launches = timed_dd(S, dd, w.descs_dev, nj, args, d, threads)
     finally:
         S.set_dd_destroy(dd)
     world = d.world
     return {
         "value": world * nj / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "lanes": lanes,
+        "submit_threads": threads,
         "p50_us": st_d["p50_us"], "p99_us": st_d["p99_us"], "submit_us": st_d["mean_launch_us"],
         "graph_launches": launches, "failed": st_d["failed"], "canary_errors": st_d["canary_errors"],
         "note": "set_dd: per lane one graph WHILE {fetch -> SWITCH {scan}} looping on the device; the host "
@@ -867,8 +885,8 @@ def run_dd_study(args, d: Dist):
                               "workers": args.workers, "jobs_per_s": nj * d.world / (ms * 1e-3),
                               "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                               "mean_launch_us": st["mean_launch_us"]}), flush=True)
-    for lanes in (4, 8, 16, 32, 64):
-        arm = device_dispatch_arm(S, w, lanes, d.local, args, d)
+    for lanes, threads in ((4, 1), (8, 1), (16, 1), (32, 1), (64, 1), (64, 2), (64, 4), (128, 4)):
+        arm = device_dispatch_arm(S, w, lanes, d.local, args, d, threads)
         if d.rank == 0:
             print(json.dumps({"workload": "dd-study", "arm": "set_dd", "io": "device", "jobs_per_s": arm["value"],
                               **{k: v for k, v in arm.items() if k not in ("value", "unit", "note")}}), flush=True)
