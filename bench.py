@@ -47,7 +47,7 @@ JOB_OUT = 8 * N_ELEM + 32
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of saxpy_scan_max_kernel, mean of three
 # launches of one ncu capture (profiles/saxpy_scan_max_kernel__scan_n65536.md); reset to None
 # whenever the kernel changes until it is captured again
-SCAN_TRAFFIC_BYTES = 544171
+SCAN_TRAFFIC_BYTES = 544427
 
 
 def parse():
@@ -371,7 +371,8 @@ def run_step_dd(S, dd, descs, n, threads=1):
 
         def share(k):
             a, b = k * n // threads, (k + 1) * n // threads
-            return S.set_dd_submit_many(dd, ctypes.byref(descs, a * sz), b - a, None, None)
+            first = ctypes.cast(ctypes.addressof(descs) + a * sz, ctypes.POINTER(S.set_job_desc))
+            return S.set_dd_submit_many(dd, first, b - a, None, None)
 
         for st in pool.map(share, range(threads)):
             S.dd_check(st, "set_dd_submit_many", dd)
