@@ -422,13 +422,15 @@ def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: D
     }
 
 
-def copy_rates(S, job_in: int, job_out: int, streams: int, reps: int = 2048):
+def copy_rates(S, job_in: int, job_out: int, streams: int, reps: int = 2048, sm: bool = False):
     """Pinned copy rates (GB/s) at the job's own sizes, `streams` streams back to back, timed in C
-    (set_copy_bandwidth): H2D alone, D2H alone, and H2D + D2H together (total bytes both ways)."""
+    (set_copy_bandwidth): H2D alone, D2H alone, and H2D + D2H together (total bytes both ways); on
+    the copy engines, or (sm) by the copy kernel of set_config.sm_copies."""
     out = {}
+    base = 3 if sm else 0
     for name, nbytes, direction in (("h2d_gbs", job_in, 0), ("d2h_gbs", job_out, 1), ("bidir_total_gbs", job_in, 2)):
         g = ctypes.c_double()
-        S.check(S.set_copy_bandwidth(nbytes, streams, reps, direction, ctypes.byref(g)), "set_copy_bandwidth")
+        S.check(S.set_copy_bandwidth(nbytes, streams, reps, base + direction, ctypes.byref(g)), "set_copy_bandwidth")
         out[name] = g.value
     return out
 
@@ -536,8 +538,12 @@ def run_set(args, d: Dist):
     # UpdateGraphParams at submit (the submitting thread binds free slots) instead of at dispatch,
     # and the same pinned host buffers read and written by the kernels over the host link (no copy
     # nodes; SET_IO_MAPPED).  Skipped under a profiler: its launch list covers the headline arms.
-    ms_bind = ms_map = None
+    ms_bind = ms_map = ms_smc = None
     if not _profiler_attached():
+        # H2D and D2H by copy kernels over NVLink-C2C (set_config.sm_copies) instead of copy nodes
+        ctxc = S.create(S.default_config(io_mode=S.SET_IO_HOST, sm_copies=1, **cfg))
+        ms_smc, st_smc = timed(S, ctxc, w.descs_host, nj, args, d)
+        S.set_destroy(ctxc)
         ctxb = S.create(S.default_config(io_mode=S.SET_IO_HOST, bind_at_submit=1, **cfg))
         ms_bind, st_bind = timed(S, ctxb, w.descs_host, nj, args, d)
         S.set_destroy(ctxb)
@@ -551,6 +557,7 @@ def run_set(args, d: Dist):
 
     k_mean_us, k_med_us = kernel_time(S, w)
     rates = copy_rates(S, JOB_IN, JOB_OUT, args.streams)
+    rates_sm = copy_rates(S, JOB_IN, JOB_OUT, args.streams, sm=True) if ms_smc is not None else None
     world = d.world
     value = world * nj / (ms_dev * 1e-3)
     e2e = world * nj / (ms_host * 1e-3)
@@ -570,6 +577,10 @@ def run_set(args, d: Dist):
     sms = t.cuda.get_device_properties(dev_index).multi_processor_count
     t_sm = nj * k_exec_us * 1e-6 * 16 / sms  # 16 CTAs per job, one per SM: the share of SM time
     bound_s = max(t_h2d, t_d2h, t_bi, t_sm)
+    bound_smc_s = None
+    if rates_sm is not None:
+        bound_smc_s = max(nj * JOB_IN / (rates_sm["h2d_gbs"] * 1e9), nj * JOB_OUT / (rates_sm["d2h_gbs"] * 1e9),
+                          nj * (JOB_IN + JOB_OUT) / (rates_sm["bidir_total_gbs"] * 1e9), t_sm)
     if d.rank != 0:
         return
     line = {
@@ -594,6 +605,13 @@ def run_set(args, d: Dist):
             "p99_us": st_bind["p99_us"], "mean_update_us": st_bind["mean_update_us"],
             "mean_launch_us": st_bind["mean_launch_us"],
             "note": "UpdateGraphParams on the submitting thread (set_config.bind_at_submit)"},
+        "e2e_sm_copies": None if ms_smc is None else {
+            "value": world * nj / (ms_smc * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
+            "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_smc, "p50_us": st_smc["p50_us"],
+            "p99_us": st_smc["p99_us"], "copy_rates_gbs": rates_sm, "bound_jobs_per_s": nj / bound_smc_s,
+            "frac_of_bound": (nj / (ms_smc * 1e-3)) / (nj / bound_smc_s),
+            "note": "set_config.sm_copies: the graphs' H2D and D2H steps are copy kernels over NVLink-C2C; "
+                    "bound from the copy kernel's own rates at the job size"},
         "e2e_mapped": None if ms_map is None else {
             "value": world * nj / (ms_map * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
             "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_map, "p50_us": st_map["p50_us"],

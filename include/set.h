@@ -205,6 +205,12 @@ typedef struct {
                           job completes with SET_EDEVICE.  Slots need kGuardBytes * 4 + 1 KiB more
                           than set_job_slot_bytes.  SET_IO_HOST (the host reads the trailer), per-job
                           graphs only (not with arena_bytes or batch_max > 1).  Default 0. */
+  int sm_copies;       /* 1: a job graph's H2D and D2H steps are copy kernels (many CTAs moving 16-byte
+                          words over NVLink-C2C) instead of memcpy nodes on the copy engines, which
+                          pay a fixed setup per copy at these job sizes.  SET_IO_HOST only, per-job
+                          graphs only (not with batch_max > 1); in / out must be page-locked host
+                          memory mapped at the same address and 16-byte aligned (SET_EINVAL at
+                          submit otherwise).  Default 0 (the paper's copy nodes). */
 } set_config;
 
 typedef struct {
@@ -316,7 +322,8 @@ int set_job_kernel_count(uint32_t type, const uint32_t dims[4], int img_fused);
 
 /* Pinned-host <-> device copy bandwidth in GB/s for copies of `bytes` issued back to back,
  * round-robin over `streams` streams, `reps` copies in all.  dir 0 = H2D, 1 = D2H, 2 = H2D and
- * D2H together (bytes counted both ways).  Allocates and frees its own buffers on the current
+ * D2H together (bytes counted both ways) on the copy engines; dir 3, 4, 5 the same done by the
+ * copy kernel of set_config.sm_copies.  Allocates and frees its own buffers on the current
  * device.  Used for the pipeline bound of the measured throughput. */
 set_status set_copy_bandwidth(size_t bytes, int streams, int reps, int dir, double* gbs);
 

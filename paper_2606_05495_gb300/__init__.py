@@ -52,7 +52,7 @@ class set_config(ctypes.Structure):
                 ("pool", c_void_p), ("pool_bytes", c_size_t), ("type_mask", c_uint32), ("device", c_int),
                 ("drain_timeout_ms", c_int), ("cb_mode", c_int), ("spin_us", c_int), ("cb_every", c_int),
                 ("batch_max", c_int), ("img_ctas_per_sm", c_int), ("img_tile", c_int), ("stamps", c_int),
-                ("arena_bytes", c_size_t), ("bind_at_submit", c_int), ("guards", c_int)]
+                ("arena_bytes", c_size_t), ("bind_at_submit", c_int), ("guards", c_int), ("sm_copies", c_int)]
 
 
 class set_stats_t(ctypes.Structure):

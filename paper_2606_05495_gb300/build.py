@@ -24,7 +24,7 @@ GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_sobel_hist.cu",
               "kernels/mlp_ln.cu", "kernels/hotspot.cu", "kernels/guards.cu", "kernels/plan.cu",
-              "kernels/dev_dispatch.cu"]
+              "kernels/dev_dispatch.cu", "kernels/copy.cu"]
 CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp",
                "runtime/trace.cpp", "runtime/dev_dispatch.cpp"]
 HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "kernels/cp_async.cuh", "kernels/dev_dispatch.h",

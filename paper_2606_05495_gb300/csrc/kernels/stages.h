@@ -115,6 +115,10 @@ const void* blur_lane_func();
 unsigned blur_lane_smem(uint32_t max_w);
 const void* dd_fetch_func();
 
+// set_config.sm_copies: one copy kernel launch moving `bytes` from src to dst (both 16-byte
+// aligned and addressable by the GPU, e.g. page-locked host memory mapped at the same address).
+void plan_copy(void* dst, const void* src, size_t bytes, KernelLaunch* k);
+
 // One-time function attributes (dynamic shared memory limits, cluster sizes).
 cudaError_t kernels_init();
 cudaError_t blur_hist_init();

@@ -387,9 +387,15 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
     const cudaKernelNodeParams p = node_params(gk[0]);
     SET_CK(cudaGraphAddKernelNode(&gi.arm, gi.graph, nullptr, 0, &p));
   }
-  if (copy_in)
+  if (copy_in && cfg_.sm_copies) {  // copy kernel over NVLink-C2C (set_config.sm_copies)
+    setk::KernelLaunch ck;
+    setk::plan_copy(base + L.in_off, ph_host_, L.in_bytes, &ck);
+    const cudaKernelNodeParams p = node_params(ck);
+    SET_CK(cudaGraphAddKernelNode(&gi.h2d, gi.graph, gi.arm ? &gi.arm : nullptr, gi.arm ? 1 : 0, &p));
+  } else if (copy_in) {
     SET_CK(cudaGraphAddMemcpyNode1D(&gi.h2d, gi.graph, gi.arm ? &gi.arm : nullptr, gi.arm ? 1 : 0, base + L.in_off,
                                     src_ph, L.in_bytes, kind_in_));
+  }
   uint32_t has_dependents = 0;
   for (int k = 0; k < nk; ++k) {
     cudaGraphNode_t deps[setk::kMaxKernels];
@@ -419,8 +425,14 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
     sinks[0] = gi.check;
     ns = 1;
   }
-  if (copy_out)
+  if (copy_out && cfg_.sm_copies) {
+    setk::KernelLaunch ck;
+    setk::plan_copy(ph_host_, base + L.out_off, L.out_bytes, &ck);
+    const cudaKernelNodeParams p = node_params(ck);
+    SET_CK(cudaGraphAddKernelNode(&gi.d2h, gi.graph, sinks, ns, &p));
+  } else if (copy_out) {
     SET_CK(cudaGraphAddMemcpyNode1D(&gi.d2h, gi.graph, sinks, ns, dst_ph, base + L.out_off, L.out_bytes, kind_out_));
+  }
   if (cfg_.cb_mode == 2) {  // Algorithm 3's callback as the graph's last node, bound to this slot
     cudaHostNodeParams hp{};
     hp.fn = host_complete;
@@ -454,14 +466,26 @@ set_status CudaDevice::update(const Slot& s, const JobRec& j, GraphInst& gi, Lau
   arm_stamps(const_cast<Slot&>(s), kl, nk);
   const bool copy_in = !io_maps_in(cfg_.io_mode), copy_out = !io_maps_out(cfg_.io_mode);
   cudaError_t e = cudaSuccess;
-  if (copy_in) e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
+  setk::KernelLaunch ck;
+  if (copy_in && cfg_.sm_copies) {
+    setk::plan_copy(base + L.in_off, j.d.in, L.in_bytes, &ck);
+    const cudaKernelNodeParams p = node_params(ck);
+    e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.h2d, &p);
+  } else if (copy_in) {
+    e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.h2d, base + L.in_off, j.d.in, L.in_bytes, kind_in_);
+  }
   if (e == cudaSuccess)
     for (int k = 0; k < nk && e == cudaSuccess; ++k) {
       const cudaKernelNodeParams p = node_params(kl[k]);
       e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.kn[k], &p);
     }
-  if (e == cudaSuccess && copy_out)
+  if (e == cudaSuccess && copy_out && cfg_.sm_copies) {
+    setk::plan_copy(j.d.out, base + L.out_off, L.out_bytes, &ck);
+    const cudaKernelNodeParams p = node_params(ck);
+    e = cudaGraphExecKernelNodeSetParams(gi.exec, gi.d2h, &p);
+  } else if (e == cudaSuccess && copy_out) {
     e = cudaGraphExecMemcpyNodeSetParams1D(gi.exec, gi.d2h, j.d.out, base + L.out_off, L.out_bytes, kind_out_);
+  }
   if (e == cudaSuccess && gi.arm) {
     setk::KernelLaunch gk[2];
     setk::plan_guards(base, L, (j.d.flags & SET_F_TEST_GUARD) != 0, &gk[0], &gk[1]);
@@ -1004,7 +1028,9 @@ extern "C" set_status set_launch_job(const set_job_desc* job, const void* d_in, 
 }
 
 extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, int dir, double* gbs) {
-  if (!gbs || bytes == 0 || streams < 1 || reps < 1 || dir < 0 || dir > 2) return SET_EINVAL;
+  if (!gbs || bytes == 0 || streams < 1 || reps < 1 || dir < 0 || dir > 5) return SET_EINVAL;
+  const bool sm = dir >= 3;  // copy kernels (set_config.sm_copies) instead of the copy engines
+  const int way = dir % 3;
   std::vector<cudaStream_t> ss(streams, nullptr);
   std::vector<void*> h(2 * streams, nullptr), d(2 * streams, nullptr);
   set_status st = SET_OK;
@@ -1029,8 +1055,20 @@ extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, in
       for (int i = 1; i < streams; ++i) ok(cudaStreamWaitEvent(ss[i], e0, 0));
       for (int r = 0; r < reps; ++r) {
         const int i = r % streams;
-        if (dir != 1) ok(cudaMemcpyAsync(d[2 * i], h[2 * i], bytes, cudaMemcpyHostToDevice, ss[i]));
-        if (dir != 0) ok(cudaMemcpyAsync(h[2 * i + 1], d[2 * i + 1], bytes, cudaMemcpyDeviceToHost, ss[i]));
+        if (sm) {
+          setk::KernelLaunch k;
+          if (way != 1) {
+            setk::plan_copy(d[2 * i], h[2 * i], bytes, &k);
+            ok(cudaLaunchKernel(k.func, k.grid, k.block, k.params, 0, ss[i]));
+          }
+          if (way != 0) {
+            setk::plan_copy(h[2 * i + 1], d[2 * i + 1], bytes, &k);
+            ok(cudaLaunchKernel(k.func, k.grid, k.block, k.params, 0, ss[i]));
+          }
+          continue;
+        }
+        if (way != 1) ok(cudaMemcpyAsync(d[2 * i], h[2 * i], bytes, cudaMemcpyHostToDevice, ss[i]));
+        if (way != 0) ok(cudaMemcpyAsync(h[2 * i + 1], d[2 * i + 1], bytes, cudaMemcpyDeviceToHost, ss[i]));
       }
       for (int i = 1; i < streams; ++i) {
         cudaEvent_t ev;
@@ -1044,7 +1082,7 @@ extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, in
     }
     float ms = 0.f;
     if (ok(cudaEventElapsedTime(&ms, e0, e1)))
-      *gbs = (double)bytes * reps * (dir == 2 ? 2.0 : 1.0) / ((double)ms * 1e-3) / 1e9;
+      *gbs = (double)bytes * reps * (way == 2 ? 2.0 : 1.0) / ((double)ms * 1e-3) / 1e9;
   }
   for (int i = 0; i < streams; ++i) {
     if (ss[i]) cudaStreamDestroy(ss[i]);

@@ -64,10 +64,11 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
       cfg.io_mode < SET_IO_HOST || cfg.io_mode > SET_IO_MAPPED_OUT || cfg.cb_mode < 0 || cfg.cb_mode > 3 ||
       ((io_maps_in(cfg.io_mode) || io_maps_out(cfg.io_mode)) && cfg.batch_max > 1) ||
       cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1) ||
-      (cfg.guards && (cfg.arena_bytes || cfg.batch_max > 1 || cfg.io_mode != SET_IO_HOST))) {
+      (cfg.guards && (cfg.arena_bytes || cfg.batch_max > 1 || cfg.io_mode != SET_IO_HOST)) || cfg.sm_copies < 0 ||
+      cfg.sm_copies > 1 || (cfg.sm_copies && (cfg.io_mode != SET_IO_HOST || cfg.batch_max > 1))) {
     *err = "invalid set_config (num_streams 1..1024, num_workers 1..256, ring_depth <= 64, slot_bytes >= 4096, "
            "cb_mode 0..3, no batched form with mapped I/O or bind_at_submit; guards only with SET_IO_HOST, "
-           "without arena or batches)";
+           "without arena or batches; sm_copies 0/1, only with SET_IO_HOST and without batches)";
     return SET_EINVAL;
   }
   std::unique_ptr<Executor> ex(new Executor(cfg));
@@ -161,6 +162,11 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
   if ((io_maps_in(cfg_.io_mode) && (reinterpret_cast<uintptr_t>(d.in) & 15u)) ||
       (io_maps_out(cfg_.io_mode) && (reinterpret_cast<uintptr_t>(d.out) & 15u))) {
     *why = "mapped I/O: in/out must be 16-byte aligned (the kernels use 16-byte accesses in place)";
+    return SET_EINVAL;
+  }
+  if (cfg_.sm_copies && (!dev_->io_accessible(d.in) || !dev_->io_accessible(d.out) ||
+                         ((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u))) {
+    *why = "sm_copies: in/out must be 16-byte aligned page-locked host memory the GPU can address";
     return SET_EINVAL;
   }
   const size_t ctl = setk::slot_control_bytes(cfg_.slot_bytes);

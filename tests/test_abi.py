@@ -113,3 +113,13 @@ def test_dd_config_defaults_and_validation_without_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert S.set_dd_create(ctypes.byref(c), ctypes.byref(dd)) == S.SET_ECUDA and not dd.value
+
+
+def test_sm_copies_configurations_refused_without_gpu():
+    # checked before any CUDA call: copy kernels only for pinned host I/O of per-job graphs
+    assert S.default_config().sm_copies == 0
+    ctx = ctypes.c_void_p()
+    for bad in (dict(io_mode=S.SET_IO_DEVICE), dict(io_mode=S.SET_IO_MAPPED_IN), dict(batch_max=4), dict(sm_copies=-1)):
+        cfg = S.default_config(**dict(dict(sm_copies=1), **bad))
+        assert S.set_create_ex(ctypes.byref(cfg), ctypes.byref(ctx)) == S.SET_EINVAL
+        assert b"sm_copies" in S.set_last_error(None)
