@@ -11,11 +11,13 @@ Printed JSON line:
   value        jobs/s with job inputs and outputs resident in HBM (SET_IO_DEVICE: the graphs'
                copy nodes are device-to-device), whole job over all ranks
   e2e          the same through the C ABI with pinned host buffers (SET_IO_HOST: H2D and D2H
-               copies on the NVLink-C2C link inside the timed region)
+               inside the timed region, moved over NVLink-C2C by the copy kernels of
+               set_config.sm_copies); e2e_copy_engines: the same with the paper's memcpy nodes
   roofline     the dominant kernel (saxpy_scan_max) timed alone with CUDA events per launch over
                a > L2 working set, against the measured HBM copy bandwidth
   pipeline     the bound max(sum H2D / B_h2d, sum D2H / B_d2h, sum (H2D + D2H) / B_bidir,
-               jobs x isolated kernel time) from copy rates measured here, and e2e / bound
+               jobs x isolated kernel time) from copy rates measured here (copy kernels for e2e,
+               copy engines for e2e_copy_engines and the baselines), and e2e / bound
   baselines    single-stream launch loop and the batch-synchronous fixed-stream graph executor
                on the same jobs (pinned host buffers)
   cpu_baseline the CPU oracle on the host cores over a bounded sample of the same jobs
@@ -505,9 +507,13 @@ def run_set(args, d: Dist):
         host_cb[name] = timed(S, ctx1, w.descs_host, nj, argparse.Namespace(warmup=2, steps=min(3, args.steps)), d)
         S.set_destroy(ctx1)
 
-    # e2e: pinned host buffers, H2D/D2H inside the timed region
+    # e2e: pinned host buffers, H2D/D2H inside the timed region, moved by the copy kernels of
+    # set_config.sm_copies (the fastest way to move a 512 KiB job over NVLink-C2C, see copy_rates)
+    ctx_sm = S.create(S.default_config(io_mode=S.SET_IO_HOST, sm_copies=1, **cfg))
+    ms_host, st_host = timed(S, ctx_sm, w.descs_host, nj, args, d, clocks)
+    # the same with the paper's copy nodes on the copy engines; the baselines run on this context
     ctx = S.create(S.default_config(io_mode=S.SET_IO_HOST, **cfg))
-    ms_host, st_host = timed(S, ctx, w.descs_host, nj, args, d, clocks)
+    ms_ce, st_ce = timed(S, ctx, w.descs_host, nj, args, d, clocks)
     clk = clocks.stop()
     baselines = {}
     if not args.no_baselines:
@@ -525,25 +531,26 @@ def run_set(args, d: Dist):
     traces = {}
     tr = S.set_trace_summary()
     if not _profiler_attached() and S.set_trace_start() == S.SET_OK:
-        run_step(S, ctx, w.descs_host, nj)
+        run_step(S, ctx_sm, w.descs_host, nj)
         S.set_trace_stop(ctypes.byref(tr))
         traces["set"] = tr.as_dict()
+        if S.set_trace_start() == S.SET_OK:
+            run_step(S, ctx, w.descs_host, nj)
+            S.set_trace_stop(ctypes.byref(tr))
+            traces["set_copy_engines"] = tr.as_dict()
         if not args.no_baselines and not _profiler_attached() and S.set_trace_start() == S.SET_OK:
             st = S.set_stats_t()
             S.set_run_baseline(ctx, S.SET_BASE_BATCH_SYNC, w.descs_host, nj, ctypes.byref(st))
             S.set_trace_stop(ctypes.byref(tr))
             traces["batch_sync_graph"] = tr.as_dict()
     S.set_destroy(ctx)
+    S.set_destroy(ctx_sm)
 
     # UpdateGraphParams at submit (the submitting thread binds free slots) instead of at dispatch,
     # and the same pinned host buffers read and written by the kernels over the host link (no copy
     # nodes; SET_IO_MAPPED).  Skipped under a profiler: its launch list covers the headline arms.
-    ms_bind = ms_map = ms_smc = None
+    ms_bind = ms_map = None
     if not _profiler_attached():
-        # H2D and D2H by copy kernels over NVLink-C2C (set_config.sm_copies) instead of copy nodes
-        ctxc = S.create(S.default_config(io_mode=S.SET_IO_HOST, sm_copies=1, **cfg))
-        ms_smc, st_smc = timed(S, ctxc, w.descs_host, nj, args, d)
-        S.set_destroy(ctxc)
         ctxb = S.create(S.default_config(io_mode=S.SET_IO_HOST, bind_at_submit=1, **cfg))
         ms_bind, st_bind = timed(S, ctxb, w.descs_host, nj, args, d)
         S.set_destroy(ctxb)
@@ -557,10 +564,13 @@ def run_set(args, d: Dist):
 
     k_mean_us, k_med_us = kernel_time(S, w)
     rates = copy_rates(S, JOB_IN, JOB_OUT, args.streams)
-    rates_sm = copy_rates(S, JOB_IN, JOB_OUT, args.streams, sm=True) if ms_smc is not None else None
+    # copy kernels gain from concurrency (unlike the engines): measured over as many streams as the
+    # executor keeps jobs in flight (lanes x ring)
+    rates_sm = copy_rates(S, JOB_IN, JOB_OUT, args.streams * args.ring, sm=True)
     world = d.world
     value = world * nj / (ms_dev * 1e-3)
     e2e = world * nj / (ms_host * 1e-3)
+    e2e_ce = world * nj / (ms_ce * 1e-3)
 
     alg_bytes = 16 * N_ELEM + 32  # read x, y; write z, S; m + trailer
     achieved = alg_bytes / (k_mean_us * 1e-6) / 1e9
@@ -577,10 +587,8 @@ def run_set(args, d: Dist):
     sms = t.cuda.get_device_properties(dev_index).multi_processor_count
     t_sm = nj * k_exec_us * 1e-6 * 16 / sms  # 16 CTAs per job, one per SM: the share of SM time
     bound_s = max(t_h2d, t_d2h, t_bi, t_sm)
-    bound_smc_s = None
-    if rates_sm is not None:
-        bound_smc_s = max(nj * JOB_IN / (rates_sm["h2d_gbs"] * 1e9), nj * JOB_OUT / (rates_sm["d2h_gbs"] * 1e9),
-                          nj * (JOB_IN + JOB_OUT) / (rates_sm["bidir_total_gbs"] * 1e9), t_sm)
+    bound_sm_s = max(nj * JOB_IN / (rates_sm["h2d_gbs"] * 1e9), nj * JOB_OUT / (rates_sm["d2h_gbs"] * 1e9),
+                     nj * (JOB_IN + JOB_OUT) / (rates_sm["bidir_total_gbs"] * 1e9), t_sm)
     if d.rank != 0:
         return
     line = {
@@ -595,23 +603,24 @@ def run_set(args, d: Dist):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
                 "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
                 "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
-                "steals": st_host["steals"],
-                "host_callbacks": {k: {"value": world * nj / (v[0] * 1e-3), "p99_us": v[1]["p99_us"],
-                                       "mean_launch_us": v[1]["mean_launch_us"]} for k, v in host_cb.items()},
-                "note": "completion by polled events (cb_mode 3); host_callbacks: cudaLaunchHostFunc on a "
-                        "callback stream (cb_mode 0), one dispatch thread"},
+                "steals": st_host["steals"], "copies": "copy kernels over NVLink-C2C (set_config.sm_copies)",
+                "note": "completion by polled events (cb_mode 3); H2D and D2H of every job by the copy kernels "
+                        "of set_config.sm_copies in place of the graph's memcpy nodes"},
+        "e2e_copy_engines": {
+            "value": e2e_ce, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
+            "ms_per_step": ms_ce, "p50_us": st_ce["p50_us"], "p99_us": st_ce["p99_us"],
+            "mean_update_us": st_ce["mean_update_us"], "mean_launch_us": st_ce["mean_launch_us"],
+            "steals": st_ce["steals"],
+            "host_callbacks": {k: {"value": world * nj / (v[0] * 1e-3), "p99_us": v[1]["p99_us"],
+                                   "mean_launch_us": v[1]["mean_launch_us"]} for k, v in host_cb.items()},
+            "note": "the paper's job graph: memcpy nodes on the copy engines, polled completion; host_callbacks: "
+                    "cudaLaunchHostFunc on a callback stream (cb_mode 0), one dispatch thread; the baselines "
+                    "run on this context"},
         "e2e_bind_at_submit": None if ms_bind is None else {
             "value": world * nj / (ms_bind * 1e-3), "unit": UNIT, "ms_per_step": ms_bind,
             "p99_us": st_bind["p99_us"], "mean_update_us": st_bind["mean_update_us"],
             "mean_launch_us": st_bind["mean_launch_us"],
-            "note": "UpdateGraphParams on the submitting thread (set_config.bind_at_submit)"},
-        "e2e_sm_copies": None if ms_smc is None else {
-            "value": world * nj / (ms_smc * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
-            "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_smc, "p50_us": st_smc["p50_us"],
-            "p99_us": st_smc["p99_us"], "copy_rates_gbs": rates_sm, "bound_jobs_per_s": nj / bound_smc_s,
-            "frac_of_bound": (nj / (ms_smc * 1e-3)) / (nj / bound_smc_s),
-            "note": "set_config.sm_copies: the graphs' H2D and D2H steps are copy kernels over NVLink-C2C; "
-                    "bound from the copy kernel's own rates at the job size"},
+            "note": "UpdateGraphParams on the submitting thread (set_config.bind_at_submit), copy engines"},
         "e2e_mapped": None if ms_map is None else {
             "value": world * nj / (ms_map * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN,
             "d2h_bytes_per_step": nj * JOB_OUT, "ms_per_step": ms_map, "p50_us": st_map["p50_us"],
@@ -624,9 +633,12 @@ def run_set(args, d: Dist):
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
                      "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
                      "alg_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
-        "pipeline": {"copy_rates_gbs": rates, "bound_jobs_per_s": nj / bound_s,
-                     "e2e_frac_of_bound": (nj / (ms_host * 1e-3)) / (nj / bound_s),
-                     "terms_ms": {"h2d": t_h2d * 1e3, "d2h": t_d2h * 1e3, "bidir": t_bi * 1e3, "sm": t_sm * 1e3}},
+        "pipeline": {"copy_kernel_rates_gbs": rates_sm, "copy_kernel_streams": args.streams * args.ring,
+                     "bound_jobs_per_s": nj / bound_sm_s, "e2e_frac_of_bound": (nj / (ms_host * 1e-3)) / (nj / bound_sm_s),
+                     "copy_engine_rates_gbs": rates, "copy_engine_bound_jobs_per_s": nj / bound_s,
+                     "copy_engine_e2e_frac_of_bound": (nj / (ms_ce * 1e-3)) / (nj / bound_s),
+                     "copy_engine_terms_ms": {"h2d": t_h2d * 1e3, "d2h": t_d2h * 1e3, "bidir": t_bi * 1e3,
+                                              "sm": t_sm * 1e3}},
         "p99_us": st_host["p99_us"],
         "mean_kernel_gap_us": traces.get("set", {}).get("mean_kernel_gap_us"),
         "trace": {k: {f: v[f] for f in ("kernels", "memcpys", "span_us", "kernel_busy_us", "copy_busy_us",
@@ -635,8 +647,8 @@ def run_set(args, d: Dist):
         "baselines": baselines, "clocks": clk,
     }
     # Eq. 4: t_schedule / T_measured = 1 - T_ideal / T_measured, T_ideal = the gap-free pipeline time
-    t_ideal_ms = bound_s * 1e3
-    sched = {"set_e2e": 1 - t_ideal_ms / ms_host}
+    t_ideal_ms = bound_s * 1e3  # copy-engine arms and baselines
+    sched = {"set_e2e": 1 - bound_sm_s * 1e3 / ms_host, "set_copy_engines": 1 - t_ideal_ms / ms_ce}
     sched.update({f"set_host_callbacks_{k}": 1 - t_ideal_ms / v[0] for k, v in host_cb.items()})
     for k, v in baselines.items():
         sched[k] = 1 - v["jobs_per_s"] / (nj / bound_s)
@@ -935,6 +947,7 @@ def run_workload(args, d: Dist):
         line["set_host_callbacks_per_job"] = _rate(S, dict(cfg, cb_every=1), js.descs, n, args, d)
         line["set_device_resident"] = _rate(S, dict(polled, io_mode=S.SET_IO_DEVICE), js.descs_dev, n, args, d)
         line["set_16_streams"] = _rate(S, dict(polled, num_streams=16), js.descs, n, args, d)
+        line["set_sm_copies"] = _rate(S, dict(polled, sm_copies=1), js.descs, n, args, d)
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
         line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"])
@@ -959,6 +972,7 @@ def run_workload(args, d: Dist):
         line["set_per_job_host_callbacks"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
         if kind == 3:
             line["set_per_stage_graphs"] = _rate(S, dict(polled, img_fused=0), js.descs, n, args, d)
+        line["set_per_job_sm_copies"] = _rate(S, dict(polled, sm_copies=1), js.descs, n, args, d)
         # batched form: autotuned jobs per launch (and tile / CTAs per SM for images) in an 8 GiB arena
         # polled completion: a batch launch's host-callback chain would cost more than its copies
         bcfg = dict(cfg, cb_mode=3, ring_depth=2, batch_max=16, arena_bytes=8 << 30, slot_bytes=1 << 30)
@@ -1006,6 +1020,7 @@ def run_workload(args, d: Dist):
                           "out_bytes": js.bytes_out, "l2": "inputs > L2 (no flush needed)"}
         line["set_cb_every_8"] = _rate(S, dict(cfg, cb_every=8), js.descs, n, args, d, clocks)
         line["set_polled_2_workers"] = _rate(S, dict(cfg, cb_mode=3, num_workers=2), js.descs, n, args, d, clocks)
+        line["set_sm_copies"] = _rate(S, dict(cfg, cb_mode=3, num_workers=2, sm_copies=1), js.descs, n, args, d)
         line["set_device_resident"] = _rate(S, dict(cfg, cb_mode=3, num_workers=2, io_mode=S.SET_IO_DEVICE),
                                             js.descs_dev, n, args, d, clocks)
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
