@@ -854,20 +854,23 @@ def _kernel_only(S, js, n, launches, flags=0):
 
 def run_copy_rates(args, d: Dist):
     """Pinned host <-> device copy rates (GB/s) by copy size and stream count (set_copy_bandwidth):
-    the copy-engine side of every pipeline bound.  One JSON line per (size, streams)."""
+    the copy-engine side of every pipeline bound, and the copy kernels of set_config.sm_copies.
+    One JSON line per (mover, size, streams)."""
     import paper_2606_05495_gb300 as S
     t = _torch()
     t.cuda.set_device(d.local)
-    for size in (128 << 10, 256 << 10, 512 << 10, 2 << 20, 16 << 20, 64 << 20):
-        for streams in (1, 4, 8, 16, 32):
-            row = {"workload": "copy-rates", "bytes": size, "streams": streams}
-            reps = max(64, min(2048, (512 << 20) // size))
-            for name, dirn in (("h2d_gbs", 0), ("d2h_gbs", 1), ("bidir_total_gbs", 2)):
-                g = ctypes.c_double()
-                S.check(S.set_copy_bandwidth(size, streams, reps, dirn, ctypes.byref(g)), "set_copy_bandwidth")
-                row[name] = g.value
-            if d.rank == 0:
-                print(json.dumps(row), flush=True)
+    for mover, base in (("copy_engines", 0), ("copy_kernels", 3)):
+        for size in (64 << 10, 128 << 10, 256 << 10, 512 << 10, 2 << 20, 16 << 20, 64 << 20):
+            for streams in (1, 4, 8, 16, 32):
+                row = {"workload": "copy-rates", "mover": mover, "bytes": size, "streams": streams}
+                reps = max(64, min(2048, (512 << 20) // size))
+                for name, dirn in (("h2d_gbs", 0), ("d2h_gbs", 1), ("bidir_total_gbs", 2)):
+                    g = ctypes.c_double()
+                    S.check(S.set_copy_bandwidth(size, streams, reps, base + dirn, ctypes.byref(g)),
+                            "set_copy_bandwidth")
+                    row[name] = g.value
+                if d.rank == 0:
+                    print(json.dumps(row), flush=True)
 
 
 def run_bind_study(args, d: Dist):

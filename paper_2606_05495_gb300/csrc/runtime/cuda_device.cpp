@@ -4,6 +4,7 @@
 // the host-function callback by a completion thread that queries each lane's oldest event.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -1031,21 +1032,23 @@ extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, in
   if (!gbs || bytes == 0 || streams < 1 || reps < 1 || dir < 0 || dir > 5) return SET_EINVAL;
   const bool sm = dir >= 3;  // copy kernels (set_config.sm_copies) instead of the copy engines
   const int way = dir % 3;
+  // successive copies use distinct buffers, up to a working set of 256 MiB per direction (more
+  // than L2), so that no copy reads data an earlier one left in the GPU's cache
+  const size_t stride = (bytes + 255) & ~size_t(255);
+  const size_t nbuf = std::max<size_t>(1, std::min<size_t>((size_t)reps, ((size_t)256 << 20) / stride + 1));
   std::vector<cudaStream_t> ss(streams, nullptr);
-  std::vector<void*> h(2 * streams, nullptr), d(2 * streams, nullptr);
+  uint8_t *h_in = nullptr, *h_out = nullptr, *d_in = nullptr, *d_out = nullptr;
   set_status st = SET_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto ok = [&](cudaError_t e) {
     if (e != cudaSuccess && st == SET_OK) st = SET_ECUDA;
     return e == cudaSuccess;
   };
-  for (int i = 0; i < streams && st == SET_OK; ++i) {
-    ok(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
-    ok(cudaHostAlloc(&h[2 * i], bytes, cudaHostAllocDefault));
-    ok(cudaHostAlloc(&h[2 * i + 1], bytes, cudaHostAllocDefault));
-    ok(cudaMalloc(&d[2 * i], bytes));
-    ok(cudaMalloc(&d[2 * i + 1], bytes));
-  }
+  for (int i = 0; i < streams && st == SET_OK; ++i) ok(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+  ok(cudaHostAlloc(reinterpret_cast<void**>(&h_in), nbuf * stride, cudaHostAllocDefault));
+  ok(cudaHostAlloc(reinterpret_cast<void**>(&h_out), nbuf * stride, cudaHostAllocDefault));
+  ok(cudaMalloc(reinterpret_cast<void**>(&d_in), nbuf * stride));
+  ok(cudaMalloc(reinterpret_cast<void**>(&d_out), nbuf * stride));
   ok(cudaEventCreate(&e0));
   ok(cudaEventCreate(&e1));
   if (st == SET_OK) {
@@ -1055,20 +1058,21 @@ extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, in
       for (int i = 1; i < streams; ++i) ok(cudaStreamWaitEvent(ss[i], e0, 0));
       for (int r = 0; r < reps; ++r) {
         const int i = r % streams;
+        const size_t off = (size_t)(r % nbuf) * stride;
         if (sm) {
           setk::KernelLaunch k;
           if (way != 1) {
-            setk::plan_copy(d[2 * i], h[2 * i], bytes, &k);
+            setk::plan_copy(d_in + off, h_in + off, bytes, &k);
             ok(cudaLaunchKernel(k.func, k.grid, k.block, k.params, 0, ss[i]));
           }
           if (way != 0) {
-            setk::plan_copy(h[2 * i + 1], d[2 * i + 1], bytes, &k);
+            setk::plan_copy(h_out + off, d_out + off, bytes, &k);
             ok(cudaLaunchKernel(k.func, k.grid, k.block, k.params, 0, ss[i]));
           }
           continue;
         }
-        if (way != 1) ok(cudaMemcpyAsync(d[2 * i], h[2 * i], bytes, cudaMemcpyHostToDevice, ss[i]));
-        if (way != 0) ok(cudaMemcpyAsync(h[2 * i + 1], d[2 * i + 1], bytes, cudaMemcpyDeviceToHost, ss[i]));
+        if (way != 1) ok(cudaMemcpyAsync(d_in + off, h_in + off, bytes, cudaMemcpyHostToDevice, ss[i]));
+        if (way != 0) ok(cudaMemcpyAsync(h_out + off, d_out + off, bytes, cudaMemcpyDeviceToHost, ss[i]));
       }
       for (int i = 1; i < streams; ++i) {
         cudaEvent_t ev;
@@ -1084,13 +1088,12 @@ extern "C" set_status set_copy_bandwidth(size_t bytes, int streams, int reps, in
     if (ok(cudaEventElapsedTime(&ms, e0, e1)))
       *gbs = (double)bytes * reps * (way == 2 ? 2.0 : 1.0) / ((double)ms * 1e-3) / 1e9;
   }
-  for (int i = 0; i < streams; ++i) {
+  for (int i = 0; i < streams; ++i)
     if (ss[i]) cudaStreamDestroy(ss[i]);
-    if (h[2 * i]) cudaFreeHost(h[2 * i]);
-    if (h[2 * i + 1]) cudaFreeHost(h[2 * i + 1]);
-    if (d[2 * i]) cudaFree(d[2 * i]);
-    if (d[2 * i + 1]) cudaFree(d[2 * i + 1]);
-  }
+  if (h_in) cudaFreeHost(h_in);
+  if (h_out) cudaFreeHost(h_out);
+  if (d_in) cudaFree(d_in);
+  if (d_out) cudaFree(d_out);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return st;
