@@ -75,6 +75,8 @@ def parse():
                    default="scan",
                    help="scan (default) is the headline line; the others measure the other workloads")
     p.add_argument("--per-stage", action="store_true", help="--kernel-only on images: the three-stage chain")
+    p.add_argument("--copy-kernel", action="store_true",
+                   help="--kernel-only on scan jobs: the sm_copies copy kernel (512 KiB host -> HBM) instead")
     p.add_argument("--clock-ms", type=float, default=25.0, help="clock sampling period in timed regions")
     p.add_argument("--rates", default="1000,2000,5000,10000,20000,35000,50000", help="serve: arrival rates (jobs/s)")
     return p.parse_args()
@@ -464,9 +466,16 @@ def kernel_time(S, w: Workload, launches: int = 512):
     return statistics.mean(ts), statistics.median(ts)
 
 
-def kernel_only(S, w: Workload, launches: int):
-    """Launches the dominant kernel alone `launches` times over the resident inputs (profiling)."""
+def kernel_only(S, w: Workload, launches: int, copy_kernel: bool = False):
+    """Launches the dominant kernel alone `launches` times over the resident inputs (profiling);
+    copy_kernel: the copy kernel of set_config.sm_copies moving one job's input (512 KiB) from
+    page-locked host memory to HBM, over a 256 MiB working set (set_copy_bandwidth, 8 streams)."""
     t = _torch()
+    if copy_kernel:
+        g = ctypes.c_double()
+        S.check(S.set_copy_bandwidth(JOB_IN, 8, launches, 3, ctypes.byref(g)), "set_copy_bandwidth")
+        print(json.dumps({"kernel_only": "copy_kernel", "launches": 2 * launches, "h2d_gbs": g.value}), flush=True)
+        return
     scratch = t.zeros(S.set_job_scratch_bytes(S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), dtype=t.uint8,
                       device=w.d_in.device)
     s = t.cuda.current_stream().cuda_stream
@@ -485,7 +494,7 @@ def run_set(args, d: Dist):
     t.cuda.set_device(dev_index)
     w = Workload(S, shard(args.jobs, d.rank), dev_index)
     if args.kernel_only:
-        kernel_only(S, w, args.kernel_only)
+        kernel_only(S, w, args.kernel_only, args.copy_kernel)
         return
     nj = len(w.ids)
     cfg = dict(num_streams=args.streams, num_workers=args.workers, slot_bytes=S.set_job_slot_bytes(
