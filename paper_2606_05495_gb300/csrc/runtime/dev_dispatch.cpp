@@ -113,7 +113,7 @@ class DevDispatch {
   uint32_t pick_lane();
   set_status validate(const set_job_desc& d, setk::JobLayout* L, std::string* why) const;
   void poll_main();
-  void reap(DdLane& l, uint32_t lane, uint64_t upto);
+  void reap(DdLane& l, uint64_t upto);
   void release();
 
   set_dd_config cfg_{};
@@ -428,7 +428,7 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
   return sticky_.load() == SET_OK ? SET_OK : (set_status)sticky_.load();
 }
 
-void DevDispatch::reap(DdLane& l, uint32_t, uint64_t upto) {
+void DevDispatch::reap(DdLane& l, uint64_t upto) {
   uint64_t r = l.reaped.load(std::memory_order_relaxed);
   const uint64_t t = now_ns();
   for (; r < upto; ++r) {
@@ -457,12 +457,12 @@ void DevDispatch::poll_main() {
   for (;;) {
     const uint32_t seen = work_sig_.load();
     bool progress = false, pending = false;
-    for (uint32_t i = 0; i < lanes_.size(); ++i) {
-      DdLane& l = *lanes_[i];
+    for (auto& lp : lanes_) {
+      DdLane& l = *lp;
       const uint64_t sq = l.seq.load(std::memory_order_acquire);
       const uint64_t done = std::min(load_acq64(&l.ctl->done), sq);
       if (done > l.reaped.load(std::memory_order_relaxed)) {
-        reap(l, i, done);
+        reap(l, done);
         progress = true;
       }
       if (sq > done) {
