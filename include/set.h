@@ -143,7 +143,8 @@ typedef struct {
  *                  directly over the host link, so a job's graph has no copy nodes.  An addition
  *                  for hosts coherently attached to the GPU (NVLink-C2C); not for MLP jobs,
  *                  whose x feeds TMA loads (SET_EINVAL), nor for the batched form or baselines.
- *                  Buffers the device cannot address are rejected at submit with SET_EINVAL.
+ *                  Buffers the device cannot address, and device memory (the completion path
+ *                  reads the trailer on the host), are rejected at submit with SET_EINVAL.
  *   SET_IO_MAPPED_IN   in as SET_IO_MAPPED (no H2D node), out by the D2H copy node.
  *   SET_IO_MAPPED_OUT  in by the H2D copy node, out as SET_IO_MAPPED (the kernels store the job's
  *                  results straight into the pinned host buffer; no D2H node).  MLP jobs allowed. */

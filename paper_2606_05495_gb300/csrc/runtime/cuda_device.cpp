@@ -130,8 +130,9 @@ class CudaDevice final : public Device {
       cudaGetLastError();
       return false;
     }
-    if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;  // mapped at the same address
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    // page-locked host memory mapped at the same address; not device memory, whose trailer the
+    // completion path could not read on the host
+    return at.type == cudaMemoryTypeHost && at.devicePointer == p;
   }
   set_status run_baseline(int kind, const JobRec* jobs, size_t n, std::vector<Slot>& slots, BuddyArena* arena,
                           LogHist* lat, LaunchCost* cost, uint64_t* t0, uint64_t* t1, std::string* err) override;

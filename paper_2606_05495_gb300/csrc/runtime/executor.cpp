@@ -156,7 +156,7 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
   }
   if ((io_maps_in(cfg_.io_mode) && !dev_->io_accessible(d.in)) ||
       (io_maps_out(cfg_.io_mode) && !dev_->io_accessible(d.out))) {
-    *why = "mapped I/O: in/out must be page-locked host memory (or device memory) the GPU can address";
+    *why = "mapped I/O: in/out must be page-locked host memory the GPU can address (not device memory)";
     return SET_EINVAL;
   }
   if ((io_maps_in(cfg_.io_mode) && (reinterpret_cast<uintptr_t>(d.in) & 15u)) ||

@@ -77,7 +77,9 @@ class Device {
   virtual uint8_t* arena_base() = 0;
   // True if graphs for jobs of this type were instantiated.
   virtual bool supports(uint32_t type) const = 0;
-  // SET_IO_MAPPED: true if the device can address the host buffer p directly.
+  // SET_IO_MAPPED and sm_copies: true if p is page-locked host memory the device can address at
+  // the same address (device memory is refused: the completion path reads the trailer from the
+  // host output).
   virtual bool io_accessible(const void* p) const = 0;
   // Autotuner of the batched form (the context's workers are idle): picks jobs per launch (<=
   // max_batch) and the image kernel's tile / CTAs per SM, applies them to later launches.

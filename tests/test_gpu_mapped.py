@@ -41,6 +41,10 @@ def test_mapped_io_rejects_mlp_and_unmapped_buffers():
         d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (n,), xin.ctypes.data, out.ctypes.data, scalar=1.0)
         assert s.set_submit(ctx, ctypes.byref(d), None) == s.SET_EINVAL
         assert b"page-locked" in s.set_last_error(ctx)
+        # device memory: refused too (the completion path reads the trailer from `out` on the host)
+        j = scan_job(6, n=n, device=True)
+        assert s.set_submit(ctx, ctypes.byref(j.desc), None) == s.SET_EINVAL
+        assert b"not device memory" in s.set_last_error(ctx)
     finally:
         s.set_destroy(ctx)
 

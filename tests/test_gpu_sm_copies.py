@@ -76,6 +76,8 @@ def test_refused_configurations_and_buffers():
         d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (n,), j.hin.data_ptr(), out.data_ptr() + 8)
         assert s.set_submit(ctx, ctypes.byref(d), None) == s.SET_EINVAL  # not 16-byte aligned
         assert b"sm_copies" in s.set_last_error(ctx)
+        dj = scan_job(71, n=n, device=True)
+        assert s.set_submit(ctx, ctypes.byref(dj.desc), None) == s.SET_EINVAL  # device memory
     finally:
         s.set_destroy(ctx)
 
