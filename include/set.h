@@ -147,8 +147,20 @@ typedef struct {
  *                  reads the trailer on the host), are rejected at submit with SET_EINVAL.
  *   SET_IO_MAPPED_IN   in as SET_IO_MAPPED (no H2D node), out by the D2H copy node.
  *   SET_IO_MAPPED_OUT  in by the H2D copy node, out as SET_IO_MAPPED (the kernels store the job's
- *                  results straight into the pinned host buffer; no D2H node).  MLP jobs allowed. */
-typedef enum { SET_IO_HOST = 0, SET_IO_DEVICE = 1, SET_IO_MAPPED = 2, SET_IO_MAPPED_IN = 3, SET_IO_MAPPED_OUT = 4 } set_io_mode;
+ *                  results straight into the pinned host buffer; no D2H node).  MLP jobs allowed.
+ *   SET_IO_DEVICE_INPLACE  in / out are 16-byte aligned device buffers of the context's GPU that the
+ *                  stage kernels read and write in place: the graph is the kernel DAG alone, no
+ *                  copy nodes (the HBM-resident counterpart of SET_IO_MAPPED).  Not for MLP
+ *                  jobs, the batched form or baselines (SET_EINVAL).  The trailer stays in the
+ *                  caller's device buffer, as with SET_IO_DEVICE. */
+typedef enum {
+  SET_IO_HOST = 0,
+  SET_IO_DEVICE = 1,
+  SET_IO_MAPPED = 2,
+  SET_IO_MAPPED_IN = 3,
+  SET_IO_MAPPED_OUT = 4,
+  SET_IO_DEVICE_INPLACE = 5
+} set_io_mode;
 
 typedef struct {
   int num_streams;     /* lanes b (paper's workers), >= 1 */

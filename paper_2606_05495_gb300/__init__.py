@@ -26,7 +26,7 @@ SET_F_NONBLOCK = 0x1
 SET_F_PER_STAGE = 0x2
 SET_F_TEST_STALL = 0x100
 SET_F_TEST_GUARD = 0x200
-SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED, SET_IO_MAPPED_IN, SET_IO_MAPPED_OUT = 0, 1, 2, 3, 4
+SET_IO_HOST, SET_IO_DEVICE, SET_IO_MAPPED, SET_IO_MAPPED_IN, SET_IO_MAPPED_OUT, SET_IO_DEVICE_INPLACE = 0, 1, 2, 3, 4, 5
 SET_BASE_SYNC, SET_BASE_BATCH_SYNC = 1, 2
 SET_SERVE_SET, SET_SERVE_BATCH_SYNC = 0, 1
 SET_TRAILER_MAGIC = 0x5E7C

@@ -124,6 +124,14 @@ class CudaDevice final : public Device {
   bool supports(uint32_t type) const override {
     return type >= 1 && type <= SET_NUM_JOB_TYPES && supported_[type];
   }
+  bool io_device(const void* p) const override {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return at.type == cudaMemoryTypeDevice && at.device == cfg_.device;
+  }
   bool io_accessible(const void* p) const override {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {

@@ -61,7 +61,7 @@ set_status Executor::create(const set_config& cfg_in, Executor** out, std::strin
   normalize(cfg);
   if (!out || cfg.num_streams < 1 || cfg.num_streams > 1024 || cfg.num_workers < 1 || cfg.num_workers > 256 ||
       cfg.ring_depth > 64 || cfg.queue_capacity > (1 << 20) || cfg.slot_bytes < 4096 ||
-      cfg.io_mode < SET_IO_HOST || cfg.io_mode > SET_IO_MAPPED_OUT || cfg.cb_mode < 0 || cfg.cb_mode > 3 ||
+      cfg.io_mode < SET_IO_HOST || cfg.io_mode > SET_IO_DEVICE_INPLACE || cfg.cb_mode < 0 || cfg.cb_mode > 3 ||
       ((io_maps_in(cfg.io_mode) || io_maps_out(cfg.io_mode)) && cfg.batch_max > 1) ||
       cfg.bind_at_submit < 0 || cfg.bind_at_submit > 2 || (cfg.bind_at_submit && cfg.batch_max > 1) ||
       (cfg.guards && (cfg.arena_bytes || cfg.batch_max > 1 || cfg.io_mode != SET_IO_HOST)) || cfg.sm_copies < 0 ||
@@ -150,12 +150,23 @@ set_status Executor::validate(const set_job_desc& d, std::string* why) const {
     *why = "MLP job needs device weights in shared[0], shared[1]";
     return SET_EINVAL;
   }
-  if (io_maps_in(cfg_.io_mode) && d.type == SET_JOB_MLP_LN) {
+  if (cfg_.io_mode == SET_IO_DEVICE_INPLACE) {
+    if (d.type == SET_JOB_MLP_LN) {
+      *why = "in-place device I/O: not for MLP jobs";
+      return SET_EINVAL;
+    }
+    if (!dev_->io_device(d.in) || !dev_->io_device(d.out) ||
+        ((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u)) {
+      *why = "in-place device I/O: in/out must be 16-byte aligned device memory of the context's GPU";
+      return SET_EINVAL;
+    }
+  } else if (io_maps_in(cfg_.io_mode) && d.type == SET_JOB_MLP_LN) {
     *why = "mapped input: MLP inputs feed TMA loads and must be copied into device memory";
     return SET_EINVAL;
   }
-  if ((io_maps_in(cfg_.io_mode) && !dev_->io_accessible(d.in)) ||
-      (io_maps_out(cfg_.io_mode) && !dev_->io_accessible(d.out))) {
+  const bool host_mapped = cfg_.io_mode != SET_IO_DEVICE_INPLACE;
+  if (host_mapped && ((io_maps_in(cfg_.io_mode) && !dev_->io_accessible(d.in)) ||
+                      (io_maps_out(cfg_.io_mode) && !dev_->io_accessible(d.out)))) {
     *why = "mapped I/O: in/out must be page-locked host memory the GPU can address (not device memory)";
     return SET_EINVAL;
   }
@@ -514,7 +525,7 @@ void Executor::on_complete_group(Slot& last) {
 }
 
 int32_t Executor::check_trailer(const Slot& s, const JobRec& j) const {
-  if (cfg_.io_mode == SET_IO_DEVICE) return SET_OK;  // the trailer stays in device memory
+  if (io_out_on_device(cfg_.io_mode)) return SET_OK;  // the trailer stays in device memory
   set_trailer t;
   std::memcpy(&t, static_cast<const uint8_t*>(j.d.out) + j.d.out_bytes - sizeof(set_trailer), sizeof t);
   if (t.job_id != j.id || t.slot_gen != s.gen || (t.word >> 16) != SET_TRAILER_MAGIC) return -1000;

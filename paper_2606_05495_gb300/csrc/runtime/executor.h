@@ -81,6 +81,8 @@ class Device {
   // the same address (device memory is refused: the completion path reads the trailer from the
   // host output).
   virtual bool io_accessible(const void* p) const = 0;
+  // SET_IO_DEVICE_INPLACE: true if p is device memory of the context's GPU.
+  virtual bool io_device(const void* p) const = 0;
   // Autotuner of the batched form (the context's workers are idle): picks jobs per launch (<=
   // max_batch) and the image kernel's tile / CTAs per SM, applies them to later launches.
   virtual set_status autotune(uint32_t type, const JobRec* sample, size_t n, int max_batch, set_tune_result* out,
@@ -97,8 +99,15 @@ void note_trace_gap(double gap_us, uint64_t t_start_ns);
 bool last_trace_gap(uint64_t since_ns, double* gap_us);
 
 // Which side of a job the kernels read / write in host memory themselves (no copy node).
-inline bool io_maps_in(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_IN; }
-inline bool io_maps_out(int io_mode) { return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_OUT; }
+// The stage kernels address the caller's buffer itself (no copy node on that side).
+inline bool io_maps_in(int io_mode) {
+  return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_IN || io_mode == SET_IO_DEVICE_INPLACE;
+}
+inline bool io_maps_out(int io_mode) {
+  return io_mode == SET_IO_MAPPED || io_mode == SET_IO_MAPPED_OUT || io_mode == SET_IO_DEVICE_INPLACE;
+}
+// The job's output (and its trailer) stays in device memory.
+inline bool io_out_on_device(int io_mode) { return io_mode == SET_IO_DEVICE || io_mode == SET_IO_DEVICE_INPLACE; }
 
 // Product CUDA device; the host-simulation test library links its own factory instead.
 std::unique_ptr<Device> make_device(const set_config& cfg);

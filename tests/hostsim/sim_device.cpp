@@ -58,6 +58,7 @@ class SimDevice final : public Device {
 
   bool supports(uint32_t type) const override { return type >= 1 && type <= SET_NUM_JOB_TYPES; }
   bool io_accessible(const void*) const override { return true; }
+  bool io_device(const void*) const override { return true; }
 
   set_status launch(Slot& s, bool callback, LaunchCost* cost, std::string* err) override {
     const uint64_t k = ++launches_;
