@@ -8,8 +8,9 @@ dispatch threads, work stealing, completion detected by a thread polling each la
 launch, H2D copy, kernel, D2H copy, completion callback) until set_wait_all returns.
 
 Printed JSON line:
-  value        jobs/s with job inputs and outputs resident in HBM (SET_IO_DEVICE: the graphs'
-               copy nodes are device-to-device), whole job over all ranks
+  value        jobs/s with job inputs and outputs resident in HBM, read and written in place by
+               the kernels (SET_IO_DEVICE_INPLACE), whole job over all ranks;
+               value_device_copy_nodes: the same with device-to-device copy nodes (SET_IO_DEVICE)
   e2e          the same through the C ABI with pinned host buffers (SET_IO_HOST: H2D and D2H
                inside the timed region, moved over NVLink-C2C by the copy kernels of
                set_config.sm_copies); e2e_copy_engines: the same with the paper's memcpy nodes
@@ -501,11 +502,15 @@ def run_set(args, d: Dist):
         S.SET_JOB_SAXPY_SCAN_MAX, S.dims4(N_ELEM)), ring_depth=args.ring, cb_mode=args.cb_mode,
         cb_every=args.cb_every, device=dev_index)
 
-    # value: inputs and outputs resident in HBM
-    ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
+    # value: inputs and outputs resident in HBM, read and written in place by the kernels (the
+    # job graph is its kernel alone); then the same with device-to-device copy nodes into the slot
+    ctx_dev = S.create(S.default_config(io_mode=S.SET_IO_DEVICE_INPLACE, **cfg))
     clocks = Clocks(dev_index, args.clock_ms)
     ms_dev, st_dev = timed(S, ctx_dev, w.descs_dev, nj, args, d, clocks)
     S.set_destroy(ctx_dev)
+    ctx_dc = S.create(S.default_config(io_mode=S.SET_IO_DEVICE, **cfg))
+    ms_dc, st_dc = timed(S, ctx_dc, w.descs_dev, nj, args, d, clocks)
+    S.set_destroy(ctx_dc)
 
     # e2e with Algorithm 3's host-function callbacks (cb_mode 0, one dispatch thread): one per job
     # as written, and one per group of 8 launches of a lane
@@ -607,8 +612,14 @@ def run_set(args, d: Dist):
         "config": {"workload": "scan jobs (saxpy -> exclusive scan -> max|S|), n=65536 fp32, 4096 jobs per GPU",
                    "jobs_per_step": nj * world, "streams": args.streams, "workers": args.workers,
                    "ring_depth": args.ring, "cb_mode": args.cb_mode, "cb_every": args.cb_every, "steal": True,
-                   "io": "HBM-resident in/out (SET_IO_DEVICE)",
+                   "io": "HBM-resident in/out, read and written in place (SET_IO_DEVICE_INPLACE)",
                    "l2": "inputs 2 GiB > L2 per step (no flush needed)", "parallelism": f"replicas x{world}"},
+        "value_device_copy_nodes": {"value": world * nj / (ms_dc * 1e-3), "unit": UNIT, "ms_per_step": ms_dc,
+                                    "p99_us": st_dc["p99_us"], "mean_update_us": st_dc["mean_update_us"],
+                                    "mean_launch_us": st_dc["mean_launch_us"],
+                                    "note": "SET_IO_DEVICE: device-to-device copy nodes into the slot around "
+                                            "the kernel"},
+        "value_update_us": st_dev["mean_update_us"], "value_launch_us": st_dev["mean_launch_us"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
                 "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
                 "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
