@@ -339,6 +339,8 @@ def run_step(S, ctx, descs, n):
 
 
 def timed(S, ctx, descs, n, args, d: Dist, clocks: "Clocks | None" = None):
+    """W warm-up steps, then K steps bracketed by CUDA events (a barrier and a synchronize on both
+    sides); an event at every step boundary also gives the median step (stats["ms_step_median"])."""
     import contextlib
     t = _torch()
     for _ in range(args.warmup):
@@ -346,18 +348,20 @@ def timed(S, ctx, descs, n, args, d: Dist, clocks: "Clocks | None" = None):
     S.set_reset_stats(ctx)
     d.barrier()
     t.cuda.synchronize()
-    e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+    ev = [t.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with clocks.window() if clocks is not None else contextlib.nullcontext():
-        e0.record()
-        for _ in range(args.steps):
+        ev[0].record()
+        for k in range(args.steps):
             run_step(S, ctx, descs, n)
-        e1.record()
+            ev[k + 1].record()
         t.cuda.synchronize()
     d.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = ev[0].elapsed_time(ev[-1]) / args.steps
     st = S.set_stats_t()
     S.set_stats(ctx, ctypes.byref(st))
-    return d.max(ms), st.as_dict()
+    out = st.as_dict()
+    out["ms_step_median"] = statistics.median(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+    return d.max(ms), out
 
 
 _SUBMIT_POOLS = {}
@@ -620,8 +624,10 @@ def run_set(args, d: Dist):
                                     "note": "SET_IO_DEVICE: device-to-device copy nodes into the slot around "
                                             "the kernel"},
         "value_update_us": st_dev["mean_update_us"], "value_launch_us": st_dev["mean_launch_us"],
+        "ms_per_step_median": st_dev["ms_step_median"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nj * JOB_IN, "d2h_bytes_per_step": nj * JOB_OUT,
-                "ms_per_step": ms_host, "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
+                "ms_per_step": ms_host, "ms_per_step_median": st_host["ms_step_median"],
+                "p50_us": st_host["p50_us"], "p99_us": st_host["p99_us"],
                 "mean_update_us": st_host["mean_update_us"], "mean_launch_us": st_host["mean_launch_us"],
                 "steals": st_host["steals"], "copies": "copy kernels over NVLink-C2C (set_config.sm_copies)",
                 "note": "completion by polled events (cb_mode 3); H2D and D2H of every job by the copy kernels "
