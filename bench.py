@@ -654,7 +654,8 @@ def run_set(args, d: Dist):
             "note": "SET_IO_MAPPED: the same pinned host buffers, read and written by the kernels over "
                     "NVLink-C2C; the job graphs have no copy nodes"},
         "device_dispatch": dd_arm,
-        "gpu_launches": args.steps * nj * 1,
+        "gpu_launches": args.steps * nj * 1,  # value's timed region: one kernel node per job
+        "gpu_launches_e2e": args.steps * nj * 3,  # e2e's: copy-in kernel, stage kernel, copy-out kernel
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
                      "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
