@@ -1121,13 +1121,15 @@ def run_workload(args, d: Dist):
             # queued and launched by a dispatch thread; set_host_callbacks: that, with Algorithm 3's
             # host function on the lane stream (cb_mode 1); set_continuous_batching: dispatch threads
             # pack the image and MLP arrivals queued at that moment into one batched launch (up to 16)
-            for name, mode, cbm, bind, nw, bmax in (("set", S.SET_SERVE_SET, 3, 2, 2, 1),
-                                                    ("set_dispatch_threads", S.SET_SERVE_SET, 3, 0, 2, 1),
-                                                    ("set_continuous_batching", S.SET_SERVE_SET, 3, 0, 2, 16),
-                                                    ("set_host_callbacks", S.SET_SERVE_SET, 1, 0, 1, 1),
-                                                    ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1, 0, 1, 1)):
+            # set_sm_copies: "set" with the copies done by copy kernels (set_config.sm_copies)
+            for name, mode, cbm, bind, nw, bmax, smc in (("set", S.SET_SERVE_SET, 3, 2, 2, 1, 0),
+                                                         ("set_sm_copies", S.SET_SERVE_SET, 3, 2, 2, 1, 1),
+                                                         ("set_dispatch_threads", S.SET_SERVE_SET, 3, 0, 2, 1, 0),
+                                                         ("set_continuous_batching", S.SET_SERVE_SET, 3, 0, 2, 16, 0),
+                                                         ("set_host_callbacks", S.SET_SERVE_SET, 1, 0, 1, 1, 0),
+                                                         ("batch_sync_graph", S.SET_SERVE_BATCH_SYNC, 1, 0, 1, 1, 0)):
                 ctx = S.create(S.default_config(**dict(cfg, cb_mode=cbm, bind_at_submit=bind, num_workers=nw,
-                                                       batch_max=bmax)))
+                                                       batch_max=bmax, sm_copies=smc)))
                 st = S.set_stats_t()
                 with clocks.window():
                     S.check(S.set_serve(ctx, mode, arr, off, npool, ctypes.byref(st)), "set_serve", ctx)
