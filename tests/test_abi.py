@@ -123,3 +123,10 @@ def test_sm_copies_configurations_refused_without_gpu():
         cfg = S.default_config(**dict(dict(sm_copies=1), **bad))
         assert S.set_create_ex(ctypes.byref(cfg), ctypes.byref(ctx)) == S.SET_EINVAL
         assert b"sm_copies" in S.set_last_error(None)
+
+
+def test_copy_bandwidth_arguments_checked_without_gpu():
+    g = ctypes.c_double()
+    for args in ((0, 8, 16, 0), (1 << 20, 0, 16, 0), (1 << 20, 8, 0, 3), (1 << 20, 8, 16, 6), (1 << 20, 8, 16, -1)):
+        assert S.set_copy_bandwidth(*args, ctypes.byref(g)) == S.SET_EINVAL
+    assert S.set_copy_bandwidth(1 << 20, 8, 16, 0, None) == S.SET_EINVAL
