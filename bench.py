@@ -585,6 +585,9 @@ def run_set(args, d: Dist):
     # copy kernels gain from concurrency (unlike the engines): measured over as many streams as the
     # executor keeps jobs in flight (lanes x ring)
     rates_sm = copy_rates(S, JOB_IN, JOB_OUT, args.streams * args.ring, sm=True)
+    # the link's ceiling for the e2e roofline: both directions at once with 64 MiB copies
+    link = ctypes.c_double()
+    S.check(S.set_copy_bandwidth(64 << 20, args.streams, 16, 2, ctypes.byref(link)), "set_copy_bandwidth")
     world = d.world
     value = world * nj / (ms_dev * 1e-3)
     e2e = world * nj / (ms_host * 1e-3)
@@ -660,6 +663,11 @@ def run_set(args, d: Dist):
                      "frac": achieved / peak, "traffic": SCAN_TRAFFIC_BYTES, "kernel": "saxpy_scan_max_kernel",
                      "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
                      "alg_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "roofline_e2e": {"bound": "c2c", "kernel": "copy_kernel (with saxpy_scan_max_kernel)",
+                         "achieved": e2e * (JOB_IN + JOB_OUT) / 1e9, "peak": link.value, "unit": "GB/s",
+                         "frac": e2e * (JOB_IN + JOB_OUT) / 1e9 / link.value,
+                         "peak_source": "measured here: H2D + D2H together with 64 MiB copy-engine copies",
+                         "note": "bytes moved over NVLink-C2C per second by the e2e arm (in + out per job)"},
         "pipeline": {"copy_kernel_rates_gbs": rates_sm, "copy_kernel_streams": args.streams * args.ring,
                      "bound_jobs_per_s": nj / bound_sm_s, "e2e_frac_of_bound": (nj / (ms_host * 1e-3)) / (nj / bound_sm_s),
                      "copy_engine_rates_gbs": rates, "copy_engine_bound_jobs_per_s": nj / bound_s,
