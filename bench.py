@@ -664,8 +664,8 @@ def run_set(args, d: Dist):
                      "kernel_us_mean": k_mean_us, "kernel_us_median": k_med_us,
                      "alg_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "roofline_e2e": {"bound": "c2c", "kernel": "copy_kernel (with saxpy_scan_max_kernel)",
-                         "achieved": e2e * (JOB_IN + JOB_OUT) / 1e9, "peak": link.value, "unit": "GB/s",
-                         "frac": e2e * (JOB_IN + JOB_OUT) / 1e9 / link.value,
+                         "achieved": nj / (ms_host * 1e-3) * (JOB_IN + JOB_OUT) / 1e9, "peak": link.value,
+                         "unit": "GB/s", "frac": nj / (ms_host * 1e-3) * (JOB_IN + JOB_OUT) / 1e9 / link.value,
                          "peak_source": "measured here: H2D + D2H together with 64 MiB copy-engine copies",
                          "note": "bytes moved over NVLink-C2C per second by the e2e arm (in + out per job)"},
         "pipeline": {"copy_kernel_rates_gbs": rates_sm, "copy_kernel_streams": args.streams * args.ring,
