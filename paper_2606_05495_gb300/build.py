@@ -26,9 +26,9 @@ CU_SOURCES = ["kernels/blur_hist.cu", "kernels/saxpy_scan_max.cu", "kernels/img_
               "kernels/mlp_ln.cu", "kernels/hotspot.cu", "kernels/guards.cu", "kernels/plan.cu",
               "kernels/dev_dispatch.cu", "kernels/copy.cu"]
 CPP_SOURCES = ["runtime/executor.cpp", "runtime/layout.cpp", "runtime/cuda_device.cpp", "runtime/capi.cpp",
-               "runtime/trace.cpp", "runtime/dev_dispatch.cpp"]
+               "runtime/trace.cpp", "runtime/dev_dispatch.cpp", "runtime/dd_cuda.cpp"]
 HEADERS = ["kernels/stages.h", "kernels/params.h", "kernels/tc.cuh", "kernels/cp_async.cuh", "kernels/dev_dispatch.h",
-           "runtime/executor.h", "runtime/sync.h", "runtime/layout.h", "runtime/thread_error.h"]
+           "runtime/executor.h", "runtime/sync.h", "runtime/layout.h", "runtime/thread_error.h", "runtime/dd_backend.h"]
 
 INCLUDES = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", os.path.join(CUDA_HOME, "include")]
 NVCC_FLAGS = GENCODE + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -3,10 +3,16 @@
 // One warp.  Every wait is bounded: a lane polls its ring for at most idle_ns (and a fixed number
 // of rounds), then ends its loop; the host relaunches the lane's graph when it has work again.
 #include "dev_dispatch.h"
+
+#include <type_traits>
+
 #include "stages.h"
 
 namespace setk {
 namespace {
+
+static_assert(std::is_same<cudaGraphConditionalHandle, unsigned long long>::value,
+              "DdFetchArgs carries conditional handles as unsigned long long");
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kPollLimit = 1u << 24;  // rounds, a backstop beside the time limit

@@ -9,8 +9,6 @@
 // the SWITCH node.  No descriptor within the idle limit: it ends the loop and counts an exit.
 #pragma once
 
-#include <cuda_runtime.h>
-
 #include <cstddef>
 #include <cstdint>
 
@@ -64,8 +62,8 @@ struct DdFetchArgs {
   uint32_t depth;       // ring entries (power of two)
   uint32_t pad;
   uint64_t idle_ns;     // end the loop after this long without a descriptor
-  cudaGraphConditionalHandle loop;  // WHILE node condition
-  cudaGraphConditionalHandle kind;  // SWITCH node selector
+  unsigned long long loop;  // cudaGraphConditionalHandle of the WHILE node's condition
+  unsigned long long kind;  // cudaGraphConditionalHandle of the SWITCH node's selector
 };
 
 }  // namespace setk

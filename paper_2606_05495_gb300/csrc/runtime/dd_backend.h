@@ -1,0 +1,52 @@
+// dd_backend.h -- what the device-dispatch lanes (set_dd_*) need from the device side.
+//
+// DevDispatch (dev_dispatch.cpp) runs the host protocol: lane choice, ring entries and their
+// reuse, completion handling, relaunch of lanes whose loop has ended, shutdown.  A backend owns
+// the memory the protocol shares with the device and the lanes' loops: the CUDA backend
+// (dd_cuda.cpp) builds one graph per lane (WHILE { fetch -> SWITCH { blur | scan } }); the
+// test library's simulated backend runs each launched loop on a host thread.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../kernels/dev_dispatch.h"
+#include "set.h"
+
+namespace setrt {
+
+// One lane's structures shared with the device (host views).
+struct DdLaneMem {
+  setk::DdEntry* ring = nullptr;  // `depth` descriptors, written by the host
+  setk::DdCtl* ctl = nullptr;     // done counter and loop exits (device), stop flag (host)
+  uint32_t* cmpl = nullptr;       // completion word per ring entry (device)
+  void* scan_scratch = nullptr;   // the scan kernel's look-back state (device memory)
+};
+
+class DdBackend {
+ public:
+  virtual ~DdBackend() = default;
+  // Allocates and zeroes every lane's structures, builds the lanes' loops (not launched).
+  virtual set_status init(const set_dd_config& cfg, uint32_t depth, std::vector<DdLaneMem>* lanes,
+                          std::string* err) = 0;
+  // The job's kernel argument struct (<= kDdArgBytes) for the lane's scan scratch.
+  virtual bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, void* scan_scratch, unsigned char* args,
+                    uint32_t* args_size) = 0;
+  // True if the lanes' kernels may use p as a job buffer in place.
+  virtual bool buffer_ok(const void* p) const = 0;
+  // Launches the lane's loop, ordered after its previous launch.
+  virtual set_status launch(uint32_t lane, std::string* err) = 0;
+  // 1: every launch of the lane has completed; 0: one is still running; -1: the lane failed (err).
+  virtual int ended(uint32_t lane, std::string* err) = 0;
+  // Makes the backend's device current for the calling thread.
+  virtual void bind_thread() = 0;
+  // Frees everything (leak: keep memory a running loop may still use).
+  virtual void release(bool leak) = 0;
+};
+
+std::unique_ptr<DdBackend> make_dd_backend();
+
+}  // namespace setrt

@@ -1,9 +1,9 @@
-// dev_dispatch.cpp -- device-dispatch lanes (set_dd_* in set.h): the host side.
+// dev_dispatch.cpp -- device-dispatch lanes (set_dd_* in set.h): the host protocol.
 //
-// Per lane: a non-blocking stream, one graph WHILE { fetch -> SWITCH { blur | scan } } built and
-// uploaded once, a ring of descriptors and a completion word per entry in page-locked host memory,
-// a control line (done counter and loop exits written by the GPU, stop flag written by the host)
-// and the lane's device block (fetched arguments, scan look-back state).
+// Per lane: a ring of descriptors and a completion word per entry, a control line (done counter
+// and loop exits written by the device, stop flag written by the host) and the lane's loop, all
+// owned by a backend (dd_backend.h: the CUDA graphs of dd_cuda.cpp, or the test library's
+// simulated device).  This file makes no CUDA call.
 //
 // Submit plans the job's single stage kernel with the same planners as the executor, writes the
 // argument struct into the lane's next ring entry and publishes it with a release store of the
@@ -11,8 +11,6 @@
 // the job that used them.  The completion thread reads each lane's done counter, completes the
 // jobs behind it (status from the completion word, latency) and relaunches lanes whose loop has
 // ended while descriptors are waiting; submitters relaunch too, under the lane's mutex.
-#include <cuda_runtime.h>
-
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -24,7 +22,8 @@
 #include <vector>
 
 #include "../kernels/dev_dispatch.h"
-#include "../kernels/stages.h"
+#include "../kernels/params.h"
+#include "dd_backend.h"
 #include "executor.h"
 #include "layout.h"
 #include "set.h"
@@ -33,15 +32,6 @@
 
 namespace setrt {
 namespace {
-
-#define DD_CK(call)                                                               \
-  do {                                                                            \
-    const cudaError_t e_ = (call);                                                \
-    if (e_ != cudaSuccess) {                                                      \
-      *err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
-      return SET_ECUDA;                                                           \
-    }                                                                             \
-  } while (0)
 
 constexpr uint64_t kPollSleepNs = 5000;
 
@@ -52,34 +42,16 @@ struct DdInfo {
 };
 
 struct DdLane {
-  std::mutex mu;  // writers of this lane's ring and graph launches
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ended = nullptr;  // recorded behind each launch of the lane's graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  setk::DdEntry* ring = nullptr;  // host view
-  setk::DdCtl* ctl = nullptr;
-  uint32_t* cmpl = nullptr;
-  setk::DdLaneDev* dev = nullptr;  // device memory
-  void* scan_scratch = nullptr;
+  std::mutex mu;  // writers of this lane's ring and launches of its loop
+  DdLaneMem m;    // ring, control line, completion words, scan scratch (from the backend)
   std::unique_ptr<DdInfo[]> info;
   std::atomic<uint64_t> seq{0};       // descriptors published
   std::atomic<uint64_t> reaped{0};    // completions handled
-  std::atomic<uint32_t> launches{0};  // graph launches (changed under mu)
+  std::atomic<uint32_t> launches{0};  // loop launches (changed under mu)
 };
 
 inline uint32_t load_acq32(const uint32_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 inline uint64_t load_acq64(const uint64_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
-
-// Device memory of `device` (the lanes' kernels read and write the job's buffers in place).
-bool device_memory(const void* p, int device) {
-  cudaPointerAttributes at{};
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice && at.device == device;
-}
 
 }  // namespace
 
@@ -107,9 +79,8 @@ class DevDispatch {
   }
 
  private:
-  set_status build_lane(uint32_t i, std::string* err);
-  set_status launch_locked(DdLane& l);
-  bool maybe_relaunch_locked(DdLane& l);
+  set_status launch_locked(uint32_t i);
+  bool maybe_relaunch_locked(uint32_t i);
   uint32_t pick_lane();
   set_status validate(const set_job_desc& d, setk::JobLayout* L, std::string* why) const;
   void poll_main();
@@ -118,9 +89,8 @@ class DevDispatch {
 
   set_dd_config cfg_{};
   uint32_t depth_ = 0, mask_ = 0;
+  std::unique_ptr<DdBackend> be_;
   std::vector<std::unique_ptr<DdLane>> lanes_;
-  void* host_block_ = nullptr;
-  void* dev_block_ = nullptr;
   bool leak_ = false;  // a lane did not end: keep its memory
   std::atomic<uint64_t> next_id_{1};
   std::atomic<uint64_t> submitted_{0}, completed_{0}, failed_{0}, canary_{0}, ring_waits_{0};
@@ -145,170 +115,44 @@ set_status DevDispatch::init(const set_dd_config& cfg, std::string* err) {
   }
   depth_ = (uint32_t)next_pow2((size_t)cfg.ring_depth);
   mask_ = depth_ - 1;
-  DD_CK(cudaSetDevice(cfg.device));
-  DD_CK(cudaFree(nullptr));
-  DD_CK(setk::kernels_init());
-
-  const uint32_t nl = (uint32_t)cfg.num_lanes;
-  const size_t ring_bytes = (size_t)depth_ * sizeof(setk::DdEntry);
-  const size_t cmpl_bytes = setk::align256((size_t)depth_ * sizeof(uint32_t));
-  const size_t host_lane = ring_bytes + sizeof(setk::DdCtl) + cmpl_bytes;
-  const size_t host_total = host_lane * nl;
-  if (cudaHostAlloc(&host_block_, host_total, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
-    cudaGetLastError();
-    host_block_ = nullptr;
-    *err = "cudaHostAlloc of the descriptor rings failed (" + std::to_string(host_total) + " bytes)";
-    return SET_ENOMEM;
-  }
-  std::memset(host_block_, 0, host_total);
-  void* host_dev = nullptr;
-  DD_CK(cudaHostGetDevicePointer(&host_dev, host_block_, 0));
-
-  setk::JobLayout SL;
-  const uint32_t sd[4] = {cfg.scan_max_n, 0, 0, 0};
-  if (!setk::job_sizes(SET_JOB_SAXPY_SCAN_MAX, sd, &SL)) {
-    *err = "scan_max_n rejected by the scan layout";
-    return SET_EINVAL;
-  }
-  const size_t lane_dev = setk::align256(sizeof(setk::DdLaneDev));
-  const size_t scratch = setk::align256(SL.persist_bytes);
-  const size_t dev_total = (lane_dev + scratch) * nl;
-  if (cudaMalloc(&dev_block_, dev_total) != cudaSuccess) {
-    cudaGetLastError();
-    dev_block_ = nullptr;
-    *err = "cudaMalloc of the lane state failed (" + std::to_string(dev_total) + " bytes)";
-    return SET_ENOMEM;
-  }
-  DD_CK(cudaMemset(dev_block_, 0, dev_total));
-
-  for (uint32_t i = 0; i < nl; ++i) {
+  be_ = make_dd_backend();
+  std::vector<DdLaneMem> mem;
+  const set_status st = be_->init(cfg, depth_, &mem, err);
+  if (st != SET_OK) return st;
+  for (const DdLaneMem& m : mem) {
     auto l = std::make_unique<DdLane>();
-    uint8_t* hb = static_cast<uint8_t*>(host_block_) + host_lane * i;
-    l->ring = reinterpret_cast<setk::DdEntry*>(hb);
-    l->ctl = reinterpret_cast<setk::DdCtl*>(hb + ring_bytes);
-    l->cmpl = reinterpret_cast<uint32_t*>(hb + ring_bytes + sizeof(setk::DdCtl));
-    uint8_t* db = static_cast<uint8_t*>(dev_block_);
-    l->dev = reinterpret_cast<setk::DdLaneDev*>(db + lane_dev * i);
-    l->scan_scratch = db + lane_dev * nl + scratch * i;
+    l->m = m;
     l->info.reset(new DdInfo[depth_]);
     lanes_.push_back(std::move(l));
   }
-  for (uint32_t i = 0; i < nl; ++i) {
-    const set_status st = build_lane(i, err);
-    if (st != SET_OK) return st;
-  }
-  DD_CK(cudaDeviceSynchronize());  // uploads and memsets done before the first descriptor
   t_reset_.store(now_ns());
   poller_ = std::thread([this] { poll_main(); });
   return SET_OK;
 }
 
-// WHILE (loop, 1 at each launch) { fetch -> SWITCH (kind) { [0] blur, [1] scan } }
-set_status DevDispatch::build_lane(uint32_t i, std::string* err) {
+set_status DevDispatch::launch_locked(uint32_t i) {
   DdLane& l = *lanes_[i];
-  DD_CK(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
-  DD_CK(cudaEventCreateWithFlags(&l.ended, cudaEventDisableTiming));
-  DD_CK(cudaGraphCreate(&l.graph, 0));
-  cudaGraphConditionalHandle hloop = 0, hkind = 0;
-  DD_CK(cudaGraphConditionalHandleCreate(&hloop, l.graph, 1u, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams wp{};
-  wp.type = cudaGraphNodeTypeConditional;
-  wp.conditional.handle = hloop;
-  wp.conditional.type = cudaGraphCondTypeWhile;
-  wp.conditional.size = 1;
-  cudaGraphNode_t wn = nullptr;
-  DD_CK(cudaGraphAddNode(&wn, l.graph, nullptr, nullptr, 0, &wp));
-  cudaGraph_t body = wp.conditional.phGraph_out[0];
-  // the fetch kernel sets the selector before the SWITCH node reads it in every iteration
-  DD_CK(cudaGraphConditionalHandleCreate(&hkind, body, setk::kDdKindNone, 0));
-
-  // device-usable addresses of this lane's host-side structures
-  void* ring_d = nullptr;
-  void* ctl_d = nullptr;
-  void* cmpl_d = nullptr;
-  DD_CK(cudaHostGetDevicePointer(&ring_d, l.ring, 0));
-  DD_CK(cudaHostGetDevicePointer(&ctl_d, l.ctl, 0));
-  DD_CK(cudaHostGetDevicePointer(&cmpl_d, l.cmpl, 0));
-  setk::DdFetchArgs fa{};
-  fa.lane = l.dev;
-  fa.ring = static_cast<const setk::DdEntry*>(ring_d);
-  fa.ctl = static_cast<setk::DdCtl*>(ctl_d);
-  fa.cmpl = static_cast<uint32_t*>(cmpl_d);
-  fa.depth = depth_;
-  fa.idle_ns = (uint64_t)cfg_.idle_us * 1000ull;
-  fa.loop = hloop;
-  fa.kind = hkind;
-  void* fargs[1] = {&fa};
-  cudaKernelNodeParams fp{};
-  fp.func = const_cast<void*>(setk::dd_fetch_func());
-  fp.gridDim = dim3(1);
-  fp.blockDim = dim3(32);
-  fp.kernelParams = fargs;
-  cudaGraphNode_t fn = nullptr;
-  DD_CK(cudaGraphAddKernelNode(&fn, body, nullptr, 0, &fp));
-
-  cudaGraphNodeParams sp{};
-  sp.type = cudaGraphNodeTypeConditional;
-  sp.conditional.handle = hkind;
-  sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = setk::kDdKinds;
-  cudaGraphNode_t sn = nullptr;
-  DD_CK(cudaGraphAddNode(&sn, body, &fn, nullptr, 1, &sp));
-
-  const void* blur_args = l.dev->args[setk::kDdKindBlur];
-  const void* scan_args = l.dev->args[setk::kDdKindScan];
-  void* bargs[1] = {&blur_args};
-  void* sargs[1] = {&scan_args};
-  cudaKernelNodeParams bp{};
-  bp.func = const_cast<void*>(setk::blur_lane_func());
-  bp.gridDim = dim3(8);
-  bp.blockDim = dim3(256);
-  bp.sharedMemBytes = setk::blur_lane_smem(cfg_.blur_max_w);
-  bp.kernelParams = bargs;
-  cudaGraphNode_t bn = nullptr;
-  DD_CK(cudaGraphAddKernelNode(&bn, sp.conditional.phGraph_out[setk::kDdKindBlur], nullptr, 0, &bp));
-  cudaKernelNodeParams kp{};
-  kp.func = const_cast<void*>(setk::scan_lane_func());
-  kp.gridDim = dim3(setk::scan_lane_grid(cfg_.scan_max_n));
-  kp.blockDim = dim3(256);
-  kp.kernelParams = sargs;
-  cudaGraphNode_t kn = nullptr;
-  DD_CK(cudaGraphAddKernelNode(&kn, sp.conditional.phGraph_out[setk::kDdKindScan], nullptr, 0, &kp));
-
-  DD_CK(cudaGraphInstantiate(&l.exec, l.graph, 0));
-  DD_CK(cudaGraphUpload(l.exec, l.stream));
-  return SET_OK;
-}
-
-set_status DevDispatch::launch_locked(DdLane& l) {
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != cfg_.device) cudaSetDevice(cfg_.device);
-  cudaError_t e = cudaGraphLaunch(l.exec, l.stream);
-  if (e == cudaSuccess) e = cudaEventRecord(l.ended, l.stream);
-  if (prev >= 0 && prev != cfg_.device) cudaSetDevice(prev);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(SET_ECUDA, std::string("lane graph launch: ") + cudaGetErrorString(e));
-  }
+  std::string why;
+  if (be_->launch(i, &why) != SET_OK) return fail(SET_ECUDA, why);
   l.launches.store(l.launches.load(std::memory_order_relaxed) + 1, std::memory_order_release);
   return SET_OK;
 }
 
 // A lane needs a launch when descriptors wait and every loop launched so far has ended: its
-// fetch counted the exit, and the graph has completed on the stream (the event behind the last
-// launch), so one launch of the lane's graph never waits behind another.
-bool DevDispatch::maybe_relaunch_locked(DdLane& l) {
-  if (l.seq.load(std::memory_order_acquire) <= load_acq64(&l.ctl->done)) return false;
-  if (load_acq32(&l.ctl->exits) != l.launches.load(std::memory_order_acquire)) return false;
-  const cudaError_t q = cudaEventQuery(l.ended);
-  if (q == cudaErrorNotReady) return false;
-  if (q != cudaSuccess) {
-    cudaGetLastError();
-    fail(SET_ECUDA, std::string("lane graph: ") + cudaGetErrorString(q));
+// fetch counted the exit, and the backend reports the last launch complete (for CUDA: the event
+// behind it), so one launch of a lane's loop never waits behind another.
+bool DevDispatch::maybe_relaunch_locked(uint32_t i) {
+  DdLane& l = *lanes_[i];
+  if (l.seq.load(std::memory_order_acquire) <= load_acq64(&l.m.ctl->done)) return false;
+  if (load_acq32(&l.m.ctl->exits) != l.launches.load(std::memory_order_acquire)) return false;
+  std::string why;
+  const int e = be_->ended(i, &why);
+  if (e == 0) return false;
+  if (e < 0) {
+    fail(SET_ECUDA, why);
     return false;
   }
-  return launch_locked(l) == SET_OK;
+  return launch_locked(i) == SET_OK;
 }
 
 // Shortest lane (fewest descriptors not yet handled), scanning from a rotating start so that
@@ -352,7 +196,7 @@ set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std:
     *why = "null in/out, or in_bytes/out_bytes do not match the job type's layout";
     return SET_EINVAL;
   }
-  if (!device_memory(d.in, cfg_.device) || !device_memory(d.out, cfg_.device)) {
+  if (!be_->buffer_ok(d.in) || !be_->buffer_ok(d.out)) {
     *why = "set_dd: in/out must be device memory of the object's GPU";
     return SET_EINVAL;
   }
@@ -376,19 +220,9 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
   const uint32_t li = pick_lane();
   DdLane& l = *lanes_[li];
   const uint64_t id = next_id_.fetch_add(1);
-  setk::JobPlanIn in;
-  in.type = d->type;
-  in.flags = d->flags;
-  std::memcpy(in.dims, d->dims, sizeof in.dims);
-  in.scalar = d->scalar;
-  in.d_in = d->in;
-  in.d_out = d->out;
-  in.d_persist = l.scan_scratch;
-  in.job_id = id;
-  in.slot_gen = li;
-  setk::KernelLaunch kl[setk::kMaxKernels];
-  int nk = 0;
-  if (!setk::plan_job(in, kl, &nk) || nk != 1 || kl[0].args_size > setk::kDdArgBytes)
+  alignas(16) unsigned char args[setk::kDdArgBytes];
+  uint32_t args_size = 0;
+  if (!be_->plan(*d, id, li, l.m.scan_scratch, args, &args_size))
     return fail(SET_EINVAL, "set_dd: the job does not plan to one kernel with a small argument struct");
 
   std::unique_lock<std::mutex> g(l.mu);
@@ -398,7 +232,7 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
     ring_waits_.fetch_add(1, std::memory_order_relaxed);
     const uint64_t limit = t0 + (uint64_t)cfg_.drain_timeout_ms * 1000000ull;
     while (s - l.reaped.load(std::memory_order_acquire) >= depth_) {
-      maybe_relaunch_locked(l);
+      maybe_relaunch_locked(li);
       if (sticky_.load() != SET_OK) return (set_status)sticky_.load();
       if (now_ns() > limit) return fail(SET_ETIMEDOUT, "set_dd_submit: the lane's ring stayed full");
       std::this_thread::yield();
@@ -409,18 +243,18 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
   inf.id = id;
   inf.status = d->status;
   inf.t_arrival = d->t_arrival_ns ? d->t_arrival_ns : t0;
-  setk::DdEntry& e = l.ring[k];
+  setk::DdEntry& e = l.m.ring[k];
   e.kind = d->type == SET_JOB_BLUR_HIST ? setk::kDdKindBlur : setk::kDdKindScan;
-  e.args_size = (uint32_t)kl[0].args_size;
+  e.args_size = args_size;
   e.job_id = id;
   e.trailer = reinterpret_cast<set_trailer*>(static_cast<uint8_t*>(d->out) + L.out_bytes - sizeof(set_trailer));
-  std::memcpy(e.args, kl[0].args, kl[0].args_size);
+  std::memcpy(e.args, args, args_size);
   __atomic_store_n(&e.seq, s + 1, __ATOMIC_RELEASE);
   l.seq.store(s + 1, std::memory_order_release);
   uint64_t z = 0;
   t_first_.compare_exchange_strong(z, t0);
   submitted_.fetch_add(1);
-  maybe_relaunch_locked(l);
+  maybe_relaunch_locked(li);
   g.unlock();
   work_sig_.notify(1);
   submit_ns_.fetch_add(now_ns() - t0, std::memory_order_relaxed);
@@ -434,7 +268,7 @@ void DevDispatch::reap(DdLane& l, uint64_t upto) {
   for (; r < upto; ++r) {
     const uint32_t k = (uint32_t)(r & mask_);
     const DdInfo inf = l.info[k];
-    const uint32_t w = __atomic_load_n(&l.cmpl[k], __ATOMIC_ACQUIRE);
+    const uint32_t w = __atomic_load_n(&l.m.cmpl[k], __ATOMIC_ACQUIRE);
     set_status st = SET_OK;
     if (w == 0u) {
       canary_.fetch_add(1, std::memory_order_relaxed);
@@ -452,24 +286,24 @@ void DevDispatch::reap(DdLane& l, uint64_t upto) {
 }
 
 void DevDispatch::poll_main() {
-  cudaSetDevice(cfg_.device);
+  be_->bind_thread();
   uint64_t last_progress = now_ns(), last_check = last_progress;
   for (;;) {
     const uint32_t seen = work_sig_.load();
     bool progress = false, pending = false;
-    for (auto& lp : lanes_) {
-      DdLane& l = *lp;
+    for (uint32_t i = 0; i < (uint32_t)lanes_.size(); ++i) {
+      DdLane& l = *lanes_[i];
       const uint64_t sq = l.seq.load(std::memory_order_acquire);
-      const uint64_t done = std::min(load_acq64(&l.ctl->done), sq);
+      const uint64_t done = std::min(load_acq64(&l.m.ctl->done), sq);
       if (done > l.reaped.load(std::memory_order_relaxed)) {
         reap(l, done);
         progress = true;
       }
       if (sq > done) {
         pending = true;
-        if (load_acq32(&l.ctl->exits) == l.launches.load(std::memory_order_acquire)) {
+        if (load_acq32(&l.m.ctl->exits) == l.launches.load(std::memory_order_acquire)) {
           std::unique_lock<std::mutex> g(l.mu, std::try_to_lock);
-          if (g.owns_lock()) maybe_relaunch_locked(l);
+          if (g.owns_lock()) maybe_relaunch_locked(i);
         }
       }
     }
@@ -485,14 +319,14 @@ void DevDispatch::poll_main() {
       last_progress = now_ns();
       continue;
     }
-    // a lane that stopped making progress: surface a CUDA error of its stream (a failed launch
-    // or a fault) instead of waiting for the caller's timeout
+    // a lane that stopped making progress: surface an error of its loop (a failed launch or a
+    // fault) instead of waiting for the caller's timeout
     if (t - last_check > 50ull * 1000000ull) {
       last_check = t;
-      for (auto& lp : lanes_) {
-        const cudaError_t e = cudaStreamQuery(lp->stream);
-        if (e != cudaSuccess && e != cudaErrorNotReady) {
-          fail(SET_ECUDA, std::string("lane stream: ") + cudaGetErrorString(e));
+      for (uint32_t i = 0; i < (uint32_t)lanes_.size(); ++i) {
+        std::string why;
+        if (be_->ended(i, &why) < 0) {
+          fail(SET_ECUDA, why);
           done_sig_.notify_all();
         }
       }
@@ -564,17 +398,16 @@ set_status DevDispatch::reset_stats() {
 set_status DevDispatch::shutdown() {
   stop_.store(true);
   set_status st = wait_all(cfg_.drain_timeout_ms);
-  for (auto& l : lanes_) __atomic_store_n(&l->ctl->stop, 1u, __ATOMIC_RELEASE);
-  // each loop ends at its next fetch: wait for the streams, bounded
+  for (auto& l : lanes_) __atomic_store_n(&l->m.ctl->stop, 1u, __ATOMIC_RELEASE);
+  // each loop ends at its next fetch: wait for every lane's last launch, bounded
   const uint64_t limit = now_ns() + ((uint64_t)cfg_.idle_us * 1000ull + 5000000000ull);
-  for (auto& l : lanes_) {
-    if (!l->stream) continue;
+  for (uint32_t i = 0; i < (uint32_t)lanes_.size(); ++i) {
     for (;;) {
-      const cudaError_t e = cudaStreamQuery(l->stream);
-      if (e == cudaSuccess) break;
-      if (e != cudaErrorNotReady) {
-        cudaGetLastError();
-        if (st == SET_OK) st = fail(SET_ECUDA, std::string("lane stream at destroy: ") + cudaGetErrorString(e));
+      std::string why;
+      const int e = be_->ended(i, &why);
+      if (e == 1) break;
+      if (e < 0) {
+        if (st == SET_OK) st = fail(SET_ECUDA, why);
         break;
       }
       if (now_ns() > limit) {
@@ -598,21 +431,7 @@ void DevDispatch::release() {
     work_sig_.notify_all();
     poller_.join();
   }
-  if (leak_) return;
-  for (auto& l : lanes_) {
-    if (l->ended) cudaEventDestroy(l->ended);
-    l->ended = nullptr;
-    if (l->exec) cudaGraphExecDestroy(l->exec);
-    if (l->graph) cudaGraphDestroy(l->graph);
-    if (l->stream) cudaStreamDestroy(l->stream);
-    l->exec = nullptr;
-    l->graph = nullptr;
-    l->stream = nullptr;
-  }
-  if (dev_block_) cudaFree(dev_block_);
-  if (host_block_) cudaFreeHost(host_block_);
-  dev_block_ = nullptr;
-  host_block_ = nullptr;
+  if (be_) be_->release(leak_);
 }
 
 }  // namespace setrt

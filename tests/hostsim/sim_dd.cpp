@@ -1,0 +1,153 @@
+// sim_dd.cpp -- TEST DOUBLE of the device-dispatch backend (dd_backend.h): no GPU, no arithmetic.
+//
+// Compiled only into the test library libset_hostsim.so (never into libset.so).  A launch of a
+// lane's loop starts a host thread that follows the fetch kernel's protocol on the same memory
+// layout: retire the job the previous iteration ran (completion word, then the done counter with
+// release order), poll the next ring entry's sequence word with acquire order for at most idle_us
+// (or until the stop word is set), take the job, and "run" it: wait a seeded random delay and
+// write its trailer {job id, lane, magic} -- the only bytes of the job it touches.  With no
+// descriptor the loop counts an exit (release order) and ends; the backend reports the launch
+// ended only after the thread's last access, as a stream reports a graph complete.
+//
+// Fault injection (environment, read at set_dd_create):
+//   SET_SIM_DD_DELAY_US=lo,hi     per-job delay range (default 2,20)
+//   SET_SIM_DD_BADTRAILER_EVERY=k every k-th job writes a wrong job id (a canary error)
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <random>
+#include <thread>
+#include <vector>
+
+#include "dd_backend.h"
+#include "sync.h"
+
+namespace setrt {
+namespace {
+
+struct SimLane {
+  // state the device keeps across launches (DdLaneDev's fields the protocol uses)
+  uint64_t head = 0, cur_seq = 0, cur_job = 0;
+  set_trailer* cur_trailer = nullptr;
+  uint32_t exits = 0;
+  std::thread th;
+  std::atomic<bool> running{false};
+  std::mt19937_64 rng;
+};
+
+class SimDdBackend final : public DdBackend {
+ public:
+  ~SimDdBackend() override { release(false); }
+
+  set_status init(const set_dd_config& cfg, uint32_t depth, std::vector<DdLaneMem>* lanes, std::string*) override {
+    cfg_ = cfg;
+    depth_ = depth;
+    if (const char* d = std::getenv("SET_SIM_DD_DELAY_US")) std::sscanf(d, "%ld,%ld", &lo_, &hi_);
+    if (const char* b = std::getenv("SET_SIM_DD_BADTRAILER_EVERY")) bad_every_ = std::strtol(b, nullptr, 10);
+    const uint32_t nl = (uint32_t)cfg.num_lanes;
+    lanes->assign(nl, DdLaneMem{});
+    for (uint32_t i = 0; i < nl; ++i) {
+      rings_.emplace_back(new setk::DdEntry[depth]());
+      ctls_.emplace_back(new setk::DdCtl[1]());
+      cmpls_.emplace_back(new uint32_t[depth]());
+      scratch_.emplace_back(new uint8_t[64]());
+      (*lanes)[i] = DdLaneMem{rings_[i].get(), ctls_[i].get(), cmpls_[i].get(), scratch_[i].get()};
+      lanes_.emplace_back(new SimLane);
+      lanes_[i]->rng.seed(0x5E7Dull * (i + 1));
+    }
+    return SET_OK;
+  }
+
+  bool plan(const set_job_desc&, uint64_t, uint32_t, void*, unsigned char*, uint32_t* args_size) override {
+    *args_size = 0;  // the simulated loop needs only the entry's job id and trailer
+    return true;
+  }
+  bool buffer_ok(const void* p) const override { return p != nullptr; }
+
+  set_status launch(uint32_t lane, std::string*) override {
+    SimLane& l = *lanes_[lane];
+    if (l.th.joinable()) l.th.join();  // the previous launch has ended (the protocol checked)
+    l.running.store(true, std::memory_order_release);
+    l.th = std::thread(&SimDdBackend::loop, this, lane);
+    return SET_OK;
+  }
+  int ended(uint32_t lane, std::string*) override { return lanes_[lane]->running.load(std::memory_order_acquire) ? 0 : 1; }
+  void bind_thread() override {}
+  void release(bool leak) override {
+    if (leak) leaked_ = true;
+    for (auto& l : lanes_)
+      if (l->th.joinable()) l->th.join();  // a simulated loop always ends (bounded poll)
+  }
+
+ private:
+  void loop(uint32_t lane) {
+    SimLane& l = *lanes_[lane];
+    setk::DdEntry* ring = rings_[lane].get();
+    setk::DdCtl* ctl = ctls_[lane].get();
+    uint32_t* cmpl = cmpls_[lane].get();
+    const uint32_t mask = depth_ - 1;
+    for (;;) {
+      if (l.cur_seq != 0) {  // retire the previous job
+        const uint64_t s = l.cur_seq;
+        set_trailer t;
+        std::memcpy(&t, l.cur_trailer, sizeof t);
+        uint32_t word = t.word;
+        if (t.job_id != l.cur_job || (word >> 16) != SET_TRAILER_MAGIC) word = 0u;
+        __atomic_store_n(&cmpl[(s - 1) & mask], word, __ATOMIC_RELAXED);
+        __atomic_store_n(&ctl->done, s, __ATOMIC_RELEASE);
+        l.cur_seq = 0;
+      }
+      const uint64_t want = l.head + 1;
+      setk::DdEntry& e = ring[l.head & mask];
+      const uint64_t t0 = now_ns();
+      bool found = false;
+      for (uint32_t it = 0;; ++it) {
+        if (__atomic_load_n(&e.seq, __ATOMIC_ACQUIRE) == want) {
+          found = true;
+          break;
+        }
+        if (__atomic_load_n(&ctl->stop, __ATOMIC_ACQUIRE) || now_ns() - t0 > (uint64_t)cfg_.idle_us * 1000ull) break;
+        if (it > 64) std::this_thread::yield();
+      }
+      if (!found) {
+        l.exits += 1;
+        __atomic_store_n(&ctl->exits, l.exits, __ATOMIC_RELEASE);
+        break;
+      }
+      l.head = want;
+      l.cur_seq = want;
+      l.cur_job = e.job_id;
+      l.cur_trailer = e.trailer;
+      // the job: a delay, then its trailer
+      const long us = lo_ + (hi_ > lo_ ? (long)(l.rng() % (uint64_t)(hi_ - lo_ + 1)) : 0);
+      if (us > 0) std::this_thread::sleep_for(std::chrono::microseconds(us));
+      const uint64_t k = jobs_.fetch_add(1) + 1;
+      set_trailer t;
+      t.job_id = (bad_every_ > 0 && k % (uint64_t)bad_every_ == 0) ? l.cur_job + 1000000007ull : l.cur_job;
+      t.slot_gen = lane;
+      t.word = (uint32_t)SET_TRAILER_MAGIC << 16;
+      std::memcpy(l.cur_trailer, &t, sizeof t);
+    }
+    l.running.store(false, std::memory_order_release);
+  }
+
+  set_dd_config cfg_{};
+  uint32_t depth_ = 0;
+  long lo_ = 2, hi_ = 20, bad_every_ = 0;
+  bool leaked_ = false;
+  std::atomic<uint64_t> jobs_{0};
+  std::vector<std::unique_ptr<setk::DdEntry[]>> rings_;
+  std::vector<std::unique_ptr<setk::DdCtl[]>> ctls_;
+  std::vector<std::unique_ptr<uint32_t[]>> cmpls_;
+  std::vector<std::unique_ptr<uint8_t[]>> scratch_;
+  std::vector<std::unique_ptr<SimLane>> lanes_;
+};
+
+}  // namespace
+
+std::unique_ptr<DdBackend> make_dd_backend() { return std::make_unique<SimDdBackend>(); }
+
+}  // namespace setrt

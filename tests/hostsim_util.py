@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 RT = os.path.join(ROOT, "paper_2606_05495_gb300", "csrc", "runtime")
 SIM = os.path.join(ROOT, "tests", "hostsim")
 OUT = os.path.join(SIM, "_build")
-SOURCES = [os.path.join(RT, f) for f in ("executor.cpp", "layout.cpp", "capi.cpp")] + [os.path.join(SIM, "sim_device.cpp")]
+SOURCES = ([os.path.join(RT, f) for f in ("executor.cpp", "layout.cpp", "capi.cpp", "dev_dispatch.cpp")] +
+           [os.path.join(SIM, f) for f in ("sim_device.cpp", "sim_dd.cpp")])
 FLAGS = ["-std=c++20", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", RT, "-I",
          os.path.join(ROOT, "paper_2606_05495_gb300", "csrc"), "-pthread"]
 
@@ -20,7 +21,9 @@ def _newer(target, deps):
 
 
 def _deps():
-    hdrs = [os.path.join(RT, h) for h in ("executor.h", "sync.h", "layout.h")] + [os.path.join(ROOT, "include", "set.h")]
+    hdrs = ([os.path.join(RT, h) for h in ("executor.h", "sync.h", "layout.h", "dd_backend.h")] +
+            [os.path.join(ROOT, "include", "set.h"),
+             os.path.join(ROOT, "paper_2606_05495_gb300", "csrc", "kernels", "dev_dispatch.h")])
     return SOURCES + hdrs
 
 
@@ -33,10 +36,10 @@ def build_lib() -> str:
     return so
 
 
-def build_stress(sanitizer: str) -> str:
+def build_stress(sanitizer: str, driver: str = "stress") -> str:
     os.makedirs(OUT, exist_ok=True)
-    exe = os.path.join(OUT, f"stress_{sanitizer}")
-    src = os.path.join(SIM, "stress.cpp")
+    exe = os.path.join(OUT, f"{driver}_{sanitizer}")
+    src = os.path.join(SIM, driver + ".cpp")
     if not _newer(exe, _deps() + [src]):
         subprocess.check_call(["g++", "-O1", "-g", f"-fsanitize={sanitizer}", "-o", exe + ".tmp"] + FLAGS +
                               SOURCES + [src])
