@@ -414,7 +414,7 @@ set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uin
 /* ---- device-side dispatch (a variant of the executor; set_dd_*) ----
  *
  * Moves dispatch and stage chaining onto the GPU.  Each lane is one stream running one graph:
- *   WHILE (loop) { fetch kernel -> SWITCH (kind) { blur kernel | scan kernel } }.
+ *   WHILE (loop) { fetch kernel -> SWITCH (kind) { blur kernel | scan kernel | image kernel } }.
  * set_dd_submit writes the job's descriptor (its kernel argument struct, planned on the host)
  * into a ring of the chosen lane in page-locked host memory.  The fetch kernel of each loop
  * iteration retires the job the previous iteration ran (a completion word and a counter written
@@ -425,9 +425,10 @@ set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uin
  * relaunches the lane's graph when work arrives.  The paper's executor (set_create) keeps the host
  * in the loop; this variant measures the device-side alternative.
  *
- * Limits: SET_JOB_BLUR_HIST and SET_JOB_SAXPY_SCAN_MAX only (kernels whose graph node can keep
- * one launch shape for every job of the lane: the scan node's grid covers scan_max_n, the blur
- * node's shared memory blur_max_w).  in / out must be 16-byte aligned device memory of the
+ * Limits: SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX and SET_JOB_IMG_SOBEL_HIST (single-kernel jobs
+ * whose graph node can keep one launch shape for every job of the lane: the scan node's grid
+ * covers scan_max_n, the blur node's shared memory blur_max_w, and the image node's fixed grid
+ * pulls the work items of any image size from the lane's ticket).  in / out must be 16-byte aligned device memory of the
  * object's GPU (checked at submit, SET_EINVAL otherwise); the kernels read and write them in
  * place.  Page-locked host buffers are refused: lane graphs whose kernels streamed them over the
  * host link faulted the GPU in testing (cause not found), so that combination is closed.  The

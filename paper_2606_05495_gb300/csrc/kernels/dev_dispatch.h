@@ -1,7 +1,7 @@
 // dev_dispatch.h -- memory layout shared by the host side of the device-dispatch lanes and their
 // fetch kernel.
 //
-// A lane is one stream running one graph: WHILE { fetch -> SWITCH(kind) { blur | scan } }.
+// A lane is one stream running one graph: WHILE { fetch -> SWITCH(kind) { blur | scan | image } }.
 // The host writes job descriptors into the lane's ring (page-locked host memory the GPU reads
 // over the host link); the fetch kernel of each iteration retires the job the previous iteration
 // ran (completion word and counter into host memory), waits a bounded time for the next
@@ -16,7 +16,7 @@
 
 namespace setk {
 
-constexpr uint32_t kDdKindBlur = 0, kDdKindScan = 1, kDdKinds = 2;
+constexpr uint32_t kDdKindBlur = 0, kDdKindScan = 1, kDdKindImg = 2, kDdKinds = 3;
 constexpr uint32_t kDdKindNone = 7;  // >= the SWITCH node's body count: no body runs
 constexpr size_t kDdArgBytes = 192;
 

@@ -275,7 +275,7 @@ __device__ void finish_item(const ImgJobDev& j, uint32_t (*whist)[256], uint32_t
 // Tile shapes of the fused kernel (rows x columns, 4096 outputs for 256 threads x 16 pixels); the
 // work item is a band of RB rows x up to kImgChunkCols columns.  The autotuner picks one.
 template <int RB, int TW>
-__global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs a) {
+__device__ __forceinline__ void img_fused_body(const ImgFusedArgs& a) {
   static_assert(RB * TW == kThreads * 16, "one 16-pixel segment per thread");
   constexpr int GR = RB + 6, GC = TW + 6, QR = RB + 2, QC = TW + 2, P = TW + 8;
   constexpr int RW = raw_words<GC>();
@@ -314,6 +314,17 @@ __global__ void __launch_bounds__(kThreads) img_fused_kernel(const ImgFusedArgs 
     }
     finish_item(j, whist, &s_flag);
   }
+}
+
+template <int RB, int TW>
+__global__ void __launch_bounds__(kThreads) img_fused_kernel(const __grid_constant__ ImgFusedArgs a) {
+  img_fused_body<RB, TW>(a);
+}
+
+// Device-dispatch lane kernel: a fixed grid pulls the job's work items from the lane's ticket
+// (every CTA count works for every image size); arguments of the job in flight in device memory.
+__global__ void __launch_bounds__(kThreads) img_fused_lane_kernel(const ImgFusedArgs* __restrict__ pa) {
+  img_fused_body<kRB, kTW>(*pa);
 }
 
 __global__ void __launch_bounds__(kThreads) gray_kernel(const GrayArgs a) {
@@ -447,6 +458,25 @@ int sm_count() {
 }
 
 }  // namespace
+
+const void* img_lane_func() { return reinterpret_cast<const void*>(&img_fused_lane_kernel); }
+uint32_t img_lane_grid() { return (uint32_t)sm_count() * 2; }
+
+bool plan_img_lane(const JobPlanIn& in, unsigned char* args, uint32_t* args_size) {
+  JobLayout L;
+  if (!job_sizes(SET_JOB_IMG_SOBEL_HIST, in.dims, &L)) return false;
+  ImgFusedArgs fa{};
+  fa.table = nullptr;
+  fa.hdr = static_cast<ImgHdr*>(in.d_persist);
+  fa.one = job_dev(in, L);
+  fa.njobs = 1;
+  fa.total_items = fa.one.nitems;
+  fa.direct = 0;  // items from the ticket: the lane's grid is fixed
+  static_assert(sizeof(ImgFusedArgs) <= 192, "image arguments fit a lane descriptor");
+  __builtin_memcpy(args, &fa, sizeof fa);
+  *args_size = (uint32_t)sizeof fa;
+  return true;
+}
 
 bool plan_img_sobel_hist(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk) {
   const ImgJobDev j = job_dev(in, L);

@@ -113,6 +113,10 @@ const void* scan_lane_func();
 uint32_t scan_lane_grid(uint32_t max_n);
 const void* blur_lane_func();
 unsigned blur_lane_smem(uint32_t max_w);
+const void* img_lane_func();
+uint32_t img_lane_grid();
+// The image lane kernel's argument struct (ticket mode over the lane's image state in d_persist).
+bool plan_img_lane(const JobPlanIn& in, unsigned char* args, uint32_t* args_size);
 const void* dd_fetch_func();
 
 // set_config.sm_copies: one copy kernel launch moving `bytes` from src to dst (both 16-byte

@@ -3,7 +3,7 @@
 // DevDispatch (dev_dispatch.cpp) runs the host protocol: lane choice, ring entries and their
 // reuse, completion handling, relaunch of lanes whose loop has ended, shutdown.  A backend owns
 // the memory the protocol shares with the device and the lanes' loops: the CUDA backend
-// (dd_cuda.cpp) builds one graph per lane (WHILE { fetch -> SWITCH { blur | scan } }); the
+// (dd_cuda.cpp) builds one graph per lane (WHILE { fetch -> SWITCH { blur | scan | image } }); the
 // test library's simulated backend runs each launched loop on a host thread.
 #pragma once
 
@@ -24,6 +24,7 @@ struct DdLaneMem {
   setk::DdCtl* ctl = nullptr;     // done counter and loop exits (device), stop flag (host)
   uint32_t* cmpl = nullptr;       // completion word per ring entry (device)
   void* scan_scratch = nullptr;   // the scan kernel's look-back state (device memory)
+  void* img_state = nullptr;      // the image kernel's ticket and histogram accumulator (device memory)
 };
 
 class DdBackend {
@@ -32,8 +33,8 @@ class DdBackend {
   // Allocates and zeroes every lane's structures, builds the lanes' loops (not launched).
   virtual set_status init(const set_dd_config& cfg, uint32_t depth, std::vector<DdLaneMem>* lanes,
                           std::string* err) = 0;
-  // The job's kernel argument struct (<= kDdArgBytes) for the lane's scan scratch.
-  virtual bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, void* scan_scratch, unsigned char* args,
+  // The job's kernel argument struct (<= kDdArgBytes) over the lane's kernel state.
+  virtual bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, unsigned char* args,
                     uint32_t* args_size) = 0;
   // True if the lanes' kernels may use p as a job buffer in place.
   virtual bool buffer_ok(const void* p) const = 0;

@@ -2,7 +2,7 @@
 //
 // Per lane: a non-blocking stream, an event recorded behind each launch, and one graph built and
 // uploaded once:  WHILE(loop, 1 at each launch) { fetch kernel -> SWITCH(kind) { [0] blur lane
-// kernel, [1] scan lane kernel } }.  The rings, control lines and completion words live in one
+// kernel, [1] scan lane kernel, [2] image lane kernel } }.  The rings, control lines and completion words live in one
 // page-locked host block mapped into the GPU's address space; the lanes' device blocks (fetched
 // arguments, scan look-back state) in one device allocation.
 #include <cuda_runtime.h>
@@ -63,9 +63,16 @@ class CudaDdBackend final : public DdBackend {
       *err = "scan_max_n rejected by the scan layout";
       return SET_EINVAL;
     }
+    setk::JobLayout IL;
+    const uint32_t id[4] = {1, 1, 0, 0};
+    if (!setk::job_sizes(SET_JOB_IMG_SOBEL_HIST, id, &IL)) {
+      *err = "image layout unavailable";
+      return SET_EINVAL;
+    }
     const size_t lane_dev = setk::align256(sizeof(setk::DdLaneDev));
     const size_t scratch = setk::align256(SL.persist_bytes);
-    const size_t dev_total = (lane_dev + scratch) * nl;
+    const size_t img_state = setk::align256(IL.persist_bytes);
+    const size_t dev_total = (lane_dev + scratch + img_state) * nl;
     if (cudaMalloc(&dev_block_, dev_total) != cudaSuccess) {
       cudaGetLastError();
       dev_block_ = nullptr;
@@ -83,16 +90,18 @@ class CudaDdBackend final : public DdBackend {
       m.ctl = reinterpret_cast<setk::DdCtl*>(hb + ring_bytes);
       m.cmpl = reinterpret_cast<uint32_t*>(hb + ring_bytes + sizeof(setk::DdCtl));
       m.scan_scratch = db + lane_dev * nl + scratch * i;
+      m.img_state = db + (lane_dev + scratch) * nl + img_state * i;
       lanes_[i].dev = reinterpret_cast<setk::DdLaneDev*>(db + lane_dev * i);
       const set_status st = build_lane(i, m, err);
       if (st != SET_OK) return st;
     }
+    lane_mem_ = *lanes;
     DD_CK(cudaDeviceSynchronize());  // uploads and memsets done before the first descriptor
     return SET_OK;
   }
 
-  bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, void* scan_scratch, unsigned char* args,
-            uint32_t* args_size) override {
+  bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, unsigned char* args, uint32_t* args_size) override {
+    const DdLaneMem& m = lane_mem_[lane];
     setk::JobPlanIn in;
     in.type = d.type;
     in.flags = d.flags;
@@ -100,9 +109,13 @@ class CudaDdBackend final : public DdBackend {
     in.scalar = d.scalar;
     in.d_in = d.in;
     in.d_out = d.out;
-    in.d_persist = scan_scratch;
     in.job_id = job_id;
     in.slot_gen = lane;
+    if (d.type == SET_JOB_IMG_SOBEL_HIST) {  // ticket mode over the lane's fixed grid
+      in.d_persist = m.img_state;
+      return setk::plan_img_lane(in, args, args_size);
+    }
+    in.d_persist = m.scan_scratch;
     setk::KernelLaunch kl[setk::kMaxKernels];
     int nk = 0;
     if (!setk::plan_job(in, kl, &nk) || nk != 1 || kl[0].args_size > setk::kDdArgBytes) return false;
@@ -235,6 +248,15 @@ class CudaDdBackend final : public DdBackend {
     kp.kernelParams = sargs;
     cudaGraphNode_t kn = nullptr;
     DD_CK(cudaGraphAddKernelNode(&kn, sp.conditional.phGraph_out[setk::kDdKindScan], nullptr, 0, &kp));
+    const void* img_args = l.dev->args[setk::kDdKindImg];
+    void* iargs[1] = {&img_args};
+    cudaKernelNodeParams ip{};
+    ip.func = const_cast<void*>(setk::img_lane_func());
+    ip.gridDim = dim3(setk::img_lane_grid());
+    ip.blockDim = dim3(256);
+    ip.kernelParams = iargs;
+    cudaGraphNode_t in_ = nullptr;
+    DD_CK(cudaGraphAddKernelNode(&in_, sp.conditional.phGraph_out[setk::kDdKindImg], nullptr, 0, &ip));
 
     DD_CK(cudaGraphInstantiate(&l.exec, l.graph, 0));
     DD_CK(cudaGraphUpload(l.exec, l.stream));
@@ -244,6 +266,7 @@ class CudaDdBackend final : public DdBackend {
   set_dd_config cfg_{};
   uint32_t depth_ = 0;
   std::vector<CudaLane> lanes_;
+  std::vector<DdLaneMem> lane_mem_;
   void* host_block_ = nullptr;
   void* dev_block_ = nullptr;
   bool leaked_ = false;

@@ -176,8 +176,8 @@ uint32_t DevDispatch::pick_lane() {
 }
 
 set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std::string* why) const {
-  if (d.type != SET_JOB_BLUR_HIST && d.type != SET_JOB_SAXPY_SCAN_MAX) {
-    *why = "set_dd: only SET_JOB_BLUR_HIST and SET_JOB_SAXPY_SCAN_MAX jobs";
+  if (d.type != SET_JOB_BLUR_HIST && d.type != SET_JOB_SAXPY_SCAN_MAX && d.type != SET_JOB_IMG_SOBEL_HIST) {
+    *why = "set_dd: only SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX and SET_JOB_IMG_SOBEL_HIST jobs";
     return SET_EINVAL;
   }
   if (!setk::job_sizes(d.type, d.dims, L)) {
@@ -222,7 +222,7 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
   const uint64_t id = next_id_.fetch_add(1);
   alignas(16) unsigned char args[setk::kDdArgBytes];
   uint32_t args_size = 0;
-  if (!be_->plan(*d, id, li, l.m.scan_scratch, args, &args_size))
+  if (!be_->plan(*d, id, li, args, &args_size))
     return fail(SET_EINVAL, "set_dd: the job does not plan to one kernel with a small argument struct");
 
   std::unique_lock<std::mutex> g(l.mu);
@@ -244,7 +244,9 @@ set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
   inf.status = d->status;
   inf.t_arrival = d->t_arrival_ns ? d->t_arrival_ns : t0;
   setk::DdEntry& e = l.m.ring[k];
-  e.kind = d->type == SET_JOB_BLUR_HIST ? setk::kDdKindBlur : setk::kDdKindScan;
+  e.kind = d->type == SET_JOB_BLUR_HIST ? setk::kDdKindBlur
+           : d->type == SET_JOB_SAXPY_SCAN_MAX ? setk::kDdKindScan
+                                               : setk::kDdKindImg;
   e.args_size = args_size;
   e.job_id = id;
   e.trailer = reinterpret_cast<set_trailer*>(static_cast<uint8_t*>(d->out) + L.out_bytes - sizeof(set_trailer));

@@ -54,14 +54,14 @@ class SimDdBackend final : public DdBackend {
       ctls_.emplace_back(new setk::DdCtl[1]());
       cmpls_.emplace_back(new uint32_t[depth]());
       scratch_.emplace_back(new uint8_t[64]());
-      (*lanes)[i] = DdLaneMem{rings_[i].get(), ctls_[i].get(), cmpls_[i].get(), scratch_[i].get()};
+      (*lanes)[i] = DdLaneMem{rings_[i].get(), ctls_[i].get(), cmpls_[i].get(), scratch_[i].get(), scratch_[i].get()};
       lanes_.emplace_back(new SimLane);
       lanes_[i]->rng.seed(0x5E7Dull * (i + 1));
     }
     return SET_OK;
   }
 
-  bool plan(const set_job_desc&, uint64_t, uint32_t, void*, unsigned char*, uint32_t* args_size) override {
+  bool plan(const set_job_desc&, uint64_t, uint32_t, unsigned char*, uint32_t* args_size) override {
     *args_size = 0;  // the simulated loop needs only the entry's job id and trailer
     return true;
   }

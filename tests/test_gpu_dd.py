@@ -68,9 +68,12 @@ def test_blur_jobs_hbm_resident():
 
 
 def test_mixed_kinds_and_ragged_sizes_share_lanes():
-    # one lane graph runs both kinds (SWITCH) and sizes below its fixed launch shape (spare scan
-    # blocks leave at once; the blur node's shared memory covers the widest image)
-    jobs = []
+    # one lane graph runs all three kinds (SWITCH) and sizes below its fixed launch shape (spare
+    # scan blocks leave at once; the blur node's shared memory covers the widest image; the image
+    # node's fixed grid pulls the work items of any image size from the lane's ticket)
+    from gpu_util import check_img, img_job
+    jobs = [img_job(500 + k, dims=d, device=True) for k, d in enumerate([(1, 1), (5, 3), (129, 257), (640, 480),
+                                                                          (2048, 33), (33, 2048)])]
     for k, n in enumerate([1, 2, 5, 4095, 4096, 4097, 30001, 65535, 65536, 7, 100, 8192]):
         jobs.append(scan_job(300 + k, n=n, device=True))
     for k, (W, H) in enumerate([(1, 1), (1, 9), (9, 1), (16, 16), (17, 3), (255, 257), (256, 1000), (33, 7)]):
@@ -80,7 +83,7 @@ def test_mixed_kinds_and_ragged_sizes_share_lanes():
     st, _ = run_dd(jobs, num_lanes=3, ring_depth=4)
     assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
     for j in jobs:
-        (check_blur if j.type == S().SET_JOB_BLUR_HIST else check_scan)(j)
+        {1: check_blur, 2: check_scan, 3: check_img}[j.type](j)
     check_dd_trailers(jobs, 3)
 
 
@@ -181,13 +184,13 @@ def test_full_ring_nonblocking_submit_returns_eagain():
 
 def test_rejects_what_a_lane_cannot_run():
     s, t = S(), __import__("torch")
-    from gpu_util import img_job
+    from gpu_util import hot_job
     dd = s.dd_create(s.dd_default_config(num_lanes=1, scan_max_n=8192, blur_max_w=64))
     try:
         big = scan_job(960, n=8193, device=True)
         wide = blur_job(961, W=65, H=4, device=True)
-        img = img_job(962, dims=(32, 32), device=True)
-        for j in (big, wide, img):
+        hot = hot_job(962, R=16, C=16, K=2, device=True)  # several launches per job: not a lane kind
+        for j in (big, wide, hot):
             assert s.set_dd_submit(dd, ctypes.byref(j.desc), None) == s.SET_EINVAL
         pageable_in = np.zeros(8 * 100, np.uint8)
         out = t.zeros(s.set_job_out_bytes(2, s.dims4(100)), dtype=t.uint8, device="cuda")
@@ -256,3 +259,14 @@ def test_concurrent_submitters():
         j.id = jid
         (check_blur if j.type == s.SET_JOB_BLUR_HIST else check_scan)(j)
     check_dd_trailers(jobs, 6)
+
+
+def test_image_jobs_of_the_workload_sizes():
+    # image jobs of the workload's log-uniform sizes (sides 128..2048) through 4 lanes
+    from gpu_util import check_img, img_job
+    jobs = [img_job(k, device=True) for k in range(24)]
+    st, _ = run_dd(jobs, num_lanes=4, ring_depth=4)
+    assert st["completed"] == 24 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        check_img(j)
+    check_dd_trailers(jobs, 4)

@@ -178,9 +178,10 @@ def test_refused_descriptors(sim):
     assert sim.set_dd_submit(dd, ctypes.byref(jobs.descs[0]), None) == B.SET_EINVAL  # n > scan_max_n
     assert b"scan_max_n" in sim.set_dd_last_error(dd)
     d = B.set_job_desc()
-    d.type = B.SET_JOB_IMG_SOBEL_HIST
-    d.dims = B.dims4(8, 8)
+    d.type = B.SET_JOB_HOTSPOT  # several launches per job: not a lane kind
+    d.dims = B.dims4(8, 8, 2)
     assert sim.set_dd_submit(dd, ctypes.byref(d), None) == B.SET_EINVAL
+    assert b"only" in sim.set_dd_last_error(dd)
     st, _ = stats(sim, dd)
     assert sim.set_dd_destroy(dd) == B.SET_OK and st.submitted == 0
 
