@@ -1028,6 +1028,18 @@ def run_workload(args, d: Dist):
         line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
         dev = JobSet(S, kind, range(min(n, 256)), device_copy=True)  # resident copies for the kernels alone
+        if kind == 3 and not _profiler_attached():
+            # HBM-resident image jobs: the executor (in place) against the device-dispatch lanes
+            nd = len(dev.ids)
+            line["hbm_resident"] = {"jobs": nd, "executor_inplace": _rate(
+                S, dict(polled, io_mode=S.SET_IO_DEVICE_INPLACE, num_workers=4), dev.descs_dev, nd, args, d)}
+            ddh = S.dd_create(S.dd_default_config(num_lanes=16, device=d.local))
+            try:
+                ms_dd, st_dd, _ = timed_dd(S, ddh, dev.descs_dev, nd, args, d)
+            finally:
+                S.set_dd_destroy(ddh)
+            line["hbm_resident"]["set_dd_16_lanes"] = {"jobs_per_s": nd / (ms_dd * 1e-3), "p99_us": st_dd["p99_us"],
+                                                       "failed": st_dd["failed"]}
         ts, m = _job_kernel_times(S, dev, len(dev.ids))
         if kind == 3:
             px = [W * H for (W, H) in dev.dims[:m]]
