@@ -31,11 +31,13 @@ def test_inplace_all_copyless_types(cb_mode):
 
 
 def test_inplace_headline_scan_configuration():
-    jobs = [scan_job(k, device=True) for k in range(1024)]
+    # bench.py's value arm: 4096 full-size scan jobs in HBM, 8 lanes x 4 slots, 4 dispatch threads,
+    # polled completion, read and written in place
+    jobs = [scan_job(k, device=True) for k in range(4096)]
     s = S()
-    st = run_jobs(jobs, num_streams=8, num_workers=4, ring_depth=4, cb_mode=3, io_mode=s.SET_IO_DEVICE_INPLACE,
-                  slot_bytes=s.set_job_slot_bytes(2, s.dims4(65536)))
-    assert st["completed"] == 1024 and st["failed"] == 0, st
+    st = run_jobs(jobs, timeout_s=300, num_streams=8, num_workers=4, ring_depth=4, cb_mode=3,
+                  io_mode=s.SET_IO_DEVICE_INPLACE, slot_bytes=s.set_job_slot_bytes(2, s.dims4(65536)))
+    assert st["completed"] == 4096 and st["failed"] == 0, st
     for j in jobs:
         check_scan(j)
     check_trailers(jobs, io_host=False)

@@ -17,11 +17,13 @@ def _slot(jobs, extra=0):
     return max(s.set_job_slot_bytes(j.type, s.dims4(*j.dims)) for j in jobs) + extra
 
 
-def test_scan_jobs_headline_size():
-    jobs = [scan_job(k) for k in range(512)]
-    st = run_jobs(jobs, num_streams=16, num_workers=4, ring_depth=4, cb_mode=3, sm_copies=1,
+def test_scan_jobs_in_the_benchmarked_configuration():
+    # bench.py's e2e arm: 4096 full-size scan jobs, 8 lanes x 4 slots, 4 dispatch threads, polled
+    # completion, copy kernels; every job checked against the oracle
+    jobs = [scan_job(k) for k in range(4096)]
+    st = run_jobs(jobs, timeout_s=300, num_streams=8, num_workers=4, ring_depth=4, cb_mode=3, sm_copies=1,
                   slot_bytes=_slot(jobs))
-    assert st["completed"] == 512 and st["failed"] == 0 and st["canary_errors"] == 0, st
+    assert st["completed"] == 4096 and st["failed"] == 0 and st["canary_errors"] == 0, st
     for j in jobs:
         check_scan(j)
     check_trailers(jobs)
