@@ -815,15 +815,27 @@ def _traces(S, cfg, descs, n):
     return out
 
 
-def _copy_bound(S, js, n, streams, e2e_jobs_per_s):
-    """Copy-engine bound of a workload (jobs/s) from pinned copy rates at its mean job sizes, and
-    the measured end-to-end rate as a fraction of it."""
+def _copy_bound(S, js, n, streams, e2e_jobs_per_s, sm_jobs_per_s=None, sm_streams=None):
+    """Copy bound of a workload (jobs/s) from pinned copy rates at its mean job sizes, and the
+    measured end-to-end rate as a fraction of it: copy engines for the copy-node arms; with
+    sm_jobs_per_s also the copy kernels (set_config.sm_copies, measured over sm_streams streams,
+    the jobs the arm keeps in flight) and that arm's fraction of its own bound."""
     mi, mo = js.bytes_in // n, js.bytes_out // n
+
+    def bound(rates):
+        return max(js.bytes_in / (rates["h2d_gbs"] * 1e9), js.bytes_out / (rates["d2h_gbs"] * 1e9),
+                   (js.bytes_in + js.bytes_out) / (rates["bidir_total_gbs"] * 1e9))
+
     rates = copy_rates(S, mi, mo, streams, reps=1024)
-    t = max(js.bytes_in / (rates["h2d_gbs"] * 1e9), js.bytes_out / (rates["d2h_gbs"] * 1e9),
-            (js.bytes_in + js.bytes_out) / (rates["bidir_total_gbs"] * 1e9))
-    return {"copy_rates_gbs": rates, "mean_in_bytes": mi, "mean_out_bytes": mo, "bound_jobs_per_s": n / t,
-            "e2e_frac_of_bound": e2e_jobs_per_s * t / n}
+    t = bound(rates)
+    out = {"copy_rates_gbs": rates, "mean_in_bytes": mi, "mean_out_bytes": mo, "bound_jobs_per_s": n / t,
+           "e2e_frac_of_bound": e2e_jobs_per_s * t / n}
+    if sm_jobs_per_s is not None:
+        rs = copy_rates(S, mi, mo, sm_streams or streams, reps=1024, sm=True)
+        ts = bound(rs)
+        out["copy_kernels"] = {"copy_rates_gbs": rs, "streams": sm_streams or streams, "bound_jobs_per_s": n / ts,
+                               "sm_copies_frac_of_bound": sm_jobs_per_s * ts / n}
+    return out
 
 
 def _peaks():
@@ -988,7 +1000,7 @@ def run_workload(args, d: Dist):
         line["set_sm_copies"] = _rate(S, dict(polled, sm_copies=1), js.descs, n, args, d)
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         line["single_stream_loop"] = _baseline(S, cfg, S.SET_BASE_SYNC, js.descs, n)
-        line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"])
+        line["pipeline"] = _copy_bound(S, js, n, 2, line["set"]["jobs_per_s"], line["set_sm_copies"]["jobs_per_s"], 8)
         line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
         ts, m = _job_kernel_times(S, js, n)
@@ -1024,7 +1036,7 @@ def run_workload(args, d: Dist):
                                "failed": st["failed"], "autotune": tune.as_dict()}
         line["batch_sync_graph"] = _baseline(S, cfg, S.SET_BASE_BATCH_SYNC, js.descs, n)
         best = max(line["set_per_job"]["jobs_per_s"], line["set_batched"]["jobs_per_s"])
-        line["pipeline"] = _copy_bound(S, js, n, 16, best)
+        line["pipeline"] = _copy_bound(S, js, n, 16, best, line["set_per_job_sm_copies"]["jobs_per_s"], 64)
         line["eq4_schedule_frac"] = _eq4(line, line["pipeline"]["bound_jobs_per_s"])
         line["trace"] = _traces(S, polled, js.descs, n)
         dev = JobSet(S, kind, range(min(n, 256)), device_copy=True)  # resident copies for the kernels alone
