@@ -196,3 +196,21 @@ def test_sanitizer_stress(san):
     for args in (("3000", "5", "4", "200"), ("3000", "2", "1", "50"), ("2000", "1", "1", "10")):
         r = subprocess.run([exe, *args], capture_output=True, text=True, env=env, timeout=600)
         assert r.returncode == 0, (args, r.stdout + r.stderr[-3000:])
+
+
+def test_reset_stats_keeps_jobs_in_flight_counted(sim):
+    sim.set_dd_reset_stats.argtypes = [ctypes.c_void_p]
+    jobs = Jobs(200)
+    dd = create(sim, num_lanes=2, ring_depth=4)
+    half = ctypes.cast(ctypes.addressof(jobs.descs) + 100 * ctypes.sizeof(B.set_job_desc),
+                       ctypes.POINTER(B.set_job_desc))
+    assert sim.set_dd_submit_many(dd, jobs.descs, 100, None, None) == B.SET_OK
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    assert sim.set_dd_reset_stats(dd) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert st.submitted == 0 and st.completed == 0 and st.p99_us == 0
+    assert sim.set_dd_submit_many(dd, half, 100, None, None) == B.SET_OK
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert sim.set_dd_destroy(dd) == B.SET_OK
+    assert st.submitted == 100 and st.completed == 100 and st.jobs_per_s > 0 and st.p50_us > 0
