@@ -25,8 +25,9 @@
  *   - A CUDA error inside a context is sticky: later calls on that context return SET_ECUDA and
  *     set_last_error() gives the CUDA error text.
  *   - Host input / output buffers belong to the caller and must stay valid until the job
- *     completes.  With SET_IO_HOST they must be page-locked (cudaHostAlloc or a pinned torch
- *     tensor); with SET_IO_DEVICE they must be device pointers of the context's GPU.
+ *     completes.  With SET_IO_HOST and the mapped modes they must be page-locked (cudaHostAlloc
+ *     or a pinned torch tensor); with SET_IO_DEVICE and SET_IO_DEVICE_INPLACE they must be device
+ *     pointers of the context's GPU.
  *   - Device memory of the slot pool belongs to the context, or to the caller when passed in
  *     set_config.pool / pool_bytes (for example a torch tensor).
  *   - Thread safety: set_submit, set_submit_many, set_wait_all and set_stats may be called from
