@@ -966,7 +966,7 @@ def run_dd_study(args, d: Dist):
                               "workers": args.workers, "jobs_per_s": nj * d.world / (ms * 1e-3),
                               "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                               "mean_launch_us": st["mean_launch_us"]}), flush=True)
-    for lanes, threads in ((4, 1), (8, 1), (16, 1), (32, 1), (64, 1), (64, 2), (64, 4), (128, 4)):
+    for lanes, threads in ((1, 1), (2, 1), (4, 1), (8, 1), (16, 1), (32, 1), (64, 1), (64, 2), (64, 4), (128, 4)):
         arm = device_dispatch_arm(S, w, lanes, d.local, args, d, threads)
         if d.rank == 0:
             print(json.dumps({"workload": "dd-study", "arm": "set_dd", "io": "device", "jobs_per_s": arm["value"],

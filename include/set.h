@@ -418,11 +418,13 @@ set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uin
  *   WHILE (loop) { fetch kernel -> SWITCH (kind) { blur kernel | scan kernel | image kernel } }.
  * set_dd_submit writes the job's descriptor (its kernel argument struct, planned on the host)
  * into a ring of the chosen lane in page-locked host memory.  The fetch kernel of each loop
- * iteration retires the job the previous iteration ran (a completion word and a counter written
- * to host memory, which a thread of the context reads to complete the job), waits a bounded time
- * for the next descriptor, copies its arguments into the lane's device memory and selects the
- * SWITCH body.  Per job the host writes one descriptor: no graph update, no graph launch and no
- * host callback.  A lane whose fetch sees no descriptor for idle_us ends its loop; the host
+ * iteration retires the jobs the previous iteration ran (a completion word each and a counter
+ * written to host memory, which a thread of the context reads to complete the jobs), waits a
+ * bounded time for the next descriptor, copies its arguments into the lane's device memory and
+ * selects the SWITCH body.  A scan descriptor takes with it the scan descriptors queued directly
+ * behind it (up to 8, those already published): the scan node runs them in one launch, each on a
+ * scratch area of its own.  Per job the host writes one descriptor: no graph update, no graph
+ * launch and no host callback.  A lane whose fetch sees no descriptor for idle_us ends its loop; the host
  * relaunches the lane's graph when work arrives.  The paper's executor (set_create) keeps the host
  * in the loop; this variant measures the device-side alternative.
  *

@@ -19,6 +19,10 @@ namespace setk {
 constexpr uint32_t kDdKindBlur = 0, kDdKindScan = 1, kDdKindImg = 2, kDdKinds = 3;
 constexpr uint32_t kDdKindNone = 7;  // >= the SWITCH node's body count: no body runs
 constexpr size_t kDdArgBytes = 192;
+// Scan jobs one loop iteration may take at once: consecutive scan descriptors already waiting in
+// the ring run as one launch of the scan node (a block of the lane's grid per tile of each job).
+// The job at sequence s uses the lane's scan scratch s % kDdScanBatch.
+constexpr uint32_t kDdScanBatch = 8;
 
 // One ring entry: 32 8-byte words, read by the fetch kernel's warp with one word per thread.
 // The host fills words 1..31, then stores seq (word 0) with release order.
@@ -44,14 +48,17 @@ static_assert(sizeof(DdCtl) == 64, "one line per lane");
 
 // Per-lane state in device memory, kept across launches of the lane's graph.
 struct alignas(64) DdLaneDev {
-  uint64_t head;             // descriptors fetched so far
-  uint64_t cur_seq;          // head value of the job in flight (0: none to retire)
-  uint64_t cur_job;          // its job id
-  set_trailer* cur_trailer;  // its trailer
-  uint32_t exits;            // loop exits so far (mirrors DdCtl::exits)
+  uint64_t head;       // descriptors fetched so far
+  uint64_t cur_first;  // sequence + 1 of the first job in flight (0: none to retire)
+  uint32_t cur_count;  // jobs in flight (consecutive sequences)
+  uint32_t exits;      // loop exits so far (mirrors DdCtl::exits)
+  uint32_t scan_count; // scan jobs the scan node runs this iteration (read by the scan kernel)
   uint32_t pad0;
-  uint64_t pad1[3];
-  alignas(64) unsigned char args[kDdKinds][kDdArgBytes];  // argument struct of each kind's node
+  uint64_t pad1[4];
+  uint64_t cur_job[kDdScanBatch];              // job ids in flight
+  set_trailer* cur_trailer[kDdScanBatch];      // their trailers
+  alignas(64) unsigned char args[kDdKinds][kDdArgBytes];  // blur and image node arguments
+  alignas(64) unsigned char scan_args[kDdScanBatch][kDdArgBytes];  // the scan jobs of the batch
 };
 
 struct DdFetchArgs {

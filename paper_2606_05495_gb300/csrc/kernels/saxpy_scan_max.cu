@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "../runtime/thread_error.h"
+#include "dev_dispatch.h"
 #include "stages.h"
 
 namespace setk {
@@ -280,34 +281,44 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_c
   scan_tile(p, blockIdx.x);
 }
 
-// Device-dispatch lane kernel: the graph node's grid is fixed (the lane's largest job); the
-// arguments of the job in flight sit in device memory, written by the lane's fetch kernel, and
-// blocks past the job's tile count leave at once.
-__global__ void __launch_bounds__(kThreads) saxpy_scan_max_lane_kernel(const ScanArgs* __restrict__ pa) {
-  const uint32_t T = pa->T, n = pa->n;
-  if (blockIdx.x >= T) return;
-  // arguments that do not describe a job this node can run (a tile count beyond the grid, n out
+// Device-dispatch lane kernel: the graph node's grid is fixed, kDdScanBatch groups of tmax blocks
+// (tmax = the tiles of the lane's largest job).  The lane's fetch kernel writes the arguments of
+// the `*count` scan jobs of this iteration into consecutive kDdArgBytes areas of device memory;
+// group j runs job j (block j * tmax + t is its tile t) on scratch area j (the planned scratch +
+// j * scratch_stride), and blocks past a job's tile count, or of groups past `*count`, leave at once.
+__global__ void __launch_bounds__(kThreads)
+    saxpy_scan_max_lane_kernel(const unsigned char* __restrict__ args, const uint32_t* __restrict__ count,
+                               uint32_t tmax, uint64_t scratch_stride) {
+  const uint32_t j = blockIdx.x / tmax, tile = blockIdx.x - j * tmax;
+  if (j >= *count || j >= kDdScanBatch) return;
+  ScanArgs p = *reinterpret_cast<const ScanArgs*>(args + (size_t)j * kDdArgBytes);
+  p.scratch += (size_t)j * scratch_stride;
+  const uint32_t T = p.T, n = p.n;
+  if (tile >= T) return;
+  // arguments that do not describe a job this node can run (a tile count beyond the group, n out
   // of the tiles' range, unaligned buffers) run nothing: the job's trailer stays unwritten and
   // the fetch kernel reports it
   // (x, z and the scratch start 16-byte aligned; y, S and m follow n floats later, and the
   // kernel's 16-byte accesses to them are taken only when n is a multiple of 4; the trailer
   // follows 8n + 16 bytes of output, so it is 8-byte aligned)
-  const uintptr_t al16 = reinterpret_cast<uintptr_t>(pa->x) | reinterpret_cast<uintptr_t>(pa->z) |
-                         reinterpret_cast<uintptr_t>(pa->scratch);
-  const uintptr_t al4 = reinterpret_cast<uintptr_t>(pa->y) | reinterpret_cast<uintptr_t>(pa->S) |
-                        reinterpret_cast<uintptr_t>(pa->m_out);
-  if (T > gridDim.x || n == 0 || n > T * kTile || n <= (T - 1) * kTile || (al16 & 15u) != 0 || (al4 & 3u) != 0 ||
-      (reinterpret_cast<uintptr_t>(pa->trailer) & 7u) != 0)
+  const uintptr_t al16 = reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.z) |
+                         reinterpret_cast<uintptr_t>(p.scratch);
+  const uintptr_t al4 = reinterpret_cast<uintptr_t>(p.y) | reinterpret_cast<uintptr_t>(p.S) |
+                        reinterpret_cast<uintptr_t>(p.m_out);
+  if (T > tmax || n == 0 || n > T * kTile || n <= (T - 1) * kTile || (al16 & 15u) != 0 || (al4 & 3u) != 0 ||
+      (reinterpret_cast<uintptr_t>(p.trailer) & 7u) != 0)
     return;
-  scan_tile(*pa, blockIdx.x);
+  scan_tile(p, tile);
 }
+
+static_assert(sizeof(ScanArgs) <= kDdArgBytes, "a scan job's arguments fit one lane argument area");
 
 inline uint32_t num_tiles(uint32_t n) { return (n + kTile - 1) / kTile; }
 
 }  // namespace
 
 const void* scan_lane_func() { return reinterpret_cast<const void*>(&saxpy_scan_max_lane_kernel); }
-uint32_t scan_lane_grid(uint32_t max_n) { return num_tiles(max_n); }
+uint32_t scan_lane_tiles(uint32_t max_n) { return num_tiles(max_n); }
 
 bool plan_saxpy_scan_max(const JobPlanIn& in, const JobLayout& L, KernelLaunch* kl, int* nk) {
   const uint32_t n = in.dims[0];

@@ -70,7 +70,9 @@ class CudaDdBackend final : public DdBackend {
       return SET_EINVAL;
     }
     const size_t lane_dev = setk::align256(sizeof(setk::DdLaneDev));
-    const size_t scratch = setk::align256(SL.persist_bytes);
+    // kDdScanBatch look-back areas: scan job j of a batch uses area j
+    scan_stride_ = setk::align256(SL.persist_bytes);
+    const size_t scratch = scan_stride_ * setk::kDdScanBatch;
     const size_t img_state = setk::align256(IL.persist_bytes);
     const size_t dev_total = (lane_dev + scratch + img_state) * nl;
     if (cudaMalloc(&dev_block_, dev_total) != cudaSuccess) {
@@ -230,9 +232,12 @@ class CudaDdBackend final : public DdBackend {
     DD_CK(cudaGraphAddNode(&sn, body, &fn, nullptr, 1, &sp));
 
     const void* blur_args = l.dev->args[setk::kDdKindBlur];
-    const void* scan_args = l.dev->args[setk::kDdKindScan];
+    const void* scan_args = l.dev->scan_args[0];
+    const void* scan_count = &l.dev->scan_count;
+    uint32_t scan_tmax = setk::scan_lane_tiles(cfg_.scan_max_n);
+    uint64_t scan_stride = scan_stride_;
     void* bargs[1] = {&blur_args};
-    void* sargs[1] = {&scan_args};
+    void* sargs[4] = {&scan_args, &scan_count, &scan_tmax, &scan_stride};
     cudaKernelNodeParams bp{};
     bp.func = const_cast<void*>(setk::blur_lane_func());
     bp.gridDim = dim3(8);
@@ -243,7 +248,7 @@ class CudaDdBackend final : public DdBackend {
     DD_CK(cudaGraphAddKernelNode(&bn, sp.conditional.phGraph_out[setk::kDdKindBlur], nullptr, 0, &bp));
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(setk::scan_lane_func());
-    kp.gridDim = dim3(setk::scan_lane_grid(cfg_.scan_max_n));
+    kp.gridDim = dim3(scan_tmax * setk::kDdScanBatch);
     kp.blockDim = dim3(256);
     kp.kernelParams = sargs;
     cudaGraphNode_t kn = nullptr;
@@ -269,6 +274,7 @@ class CudaDdBackend final : public DdBackend {
   std::vector<DdLaneMem> lane_mem_;
   void* host_block_ = nullptr;
   void* dev_block_ = nullptr;
+  size_t scan_stride_ = 0;  // bytes between the scan look-back areas of one lane
   bool leaked_ = false;
 };
 

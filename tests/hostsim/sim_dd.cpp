@@ -2,12 +2,14 @@
 //
 // Compiled only into the test library libset_hostsim.so (never into libset.so).  A launch of a
 // lane's loop starts a host thread that follows the fetch kernel's protocol on the same memory
-// layout: retire the job the previous iteration ran (completion word, then the done counter with
-// release order), poll the next ring entry's sequence word with acquire order for at most idle_us
-// (or until the stop word is set), take the job, and "run" it: wait a seeded random delay and
-// write its trailer {job id, lane, magic} -- the only bytes of the job it touches.  With no
-// descriptor the loop counts an exit (release order) and ends; the backend reports the launch
-// ended only after the thread's last access, as a stream reports a graph complete.
+// layout: retire the jobs the previous iteration ran (their completion words, then the done
+// counter with release order), poll the next ring entry's sequence word with acquire order for at
+// most idle_us (or until the stop word is set), take the job -- a scan job together with the scan
+// entries directly behind it that are already complete, up to kDdScanBatch, as the fetch kernel
+// does -- and "run" them: wait a seeded random delay and write each trailer {job id, lane, magic},
+// the only bytes of a job it touches.  With no descriptor the loop counts an exit (release order)
+// and ends; the backend reports the launch ended only after the thread's last access, as a stream
+// reports a graph complete.
 //
 // Fault injection (environment, read at set_dd_create):
 //   SET_SIM_DD_DELAY_US=lo,hi     per-job delay range (default 2,20)
@@ -28,11 +30,14 @@
 namespace setrt {
 namespace {
 
+std::atomic<uint64_t> g_batched_jobs{0};  // jobs that ran in batches of two or more (all objects)
+
 struct SimLane {
   // state the device keeps across launches (DdLaneDev's fields the protocol uses)
-  uint64_t head = 0, cur_seq = 0, cur_job = 0;
-  set_trailer* cur_trailer = nullptr;
-  uint32_t exits = 0;
+  uint64_t head = 0, cur_first = 0;
+  uint32_t cur_count = 0, exits = 0;
+  uint64_t cur_job[setk::kDdScanBatch] = {};
+  set_trailer* cur_trailer[setk::kDdScanBatch] = {};
   std::thread th;
   std::atomic<bool> running{false};
   std::mt19937_64 rng;
@@ -90,16 +95,15 @@ class SimDdBackend final : public DdBackend {
     uint32_t* cmpl = cmpls_[lane].get();
     const uint32_t mask = depth_ - 1;
     for (;;) {
-      if (l.cur_seq != 0) {  // retire the previous job
-        const uint64_t s = l.cur_seq;
+      for (uint32_t i = 0; i < l.cur_count; ++i) {  // retire the previous batch
         set_trailer t;
-        std::memcpy(&t, l.cur_trailer, sizeof t);
+        std::memcpy(&t, l.cur_trailer[i], sizeof t);
         uint32_t word = t.word;
-        if (t.job_id != l.cur_job || (word >> 16) != SET_TRAILER_MAGIC) word = 0u;
-        __atomic_store_n(&cmpl[(s - 1) & mask], word, __ATOMIC_RELAXED);
-        __atomic_store_n(&ctl->done, s, __ATOMIC_RELEASE);
-        l.cur_seq = 0;
+        if (t.job_id != l.cur_job[i] || (word >> 16) != SET_TRAILER_MAGIC) word = 0u;
+        __atomic_store_n(&cmpl[(l.cur_first - 1 + i) & mask], word, __ATOMIC_RELAXED);
       }
+      if (l.cur_count != 0) __atomic_store_n(&ctl->done, l.cur_first + l.cur_count - 1, __ATOMIC_RELEASE);
+      l.cur_count = 0;
       const uint64_t want = l.head + 1;
       setk::DdEntry& e = ring[l.head & mask];
       const uint64_t t0 = now_ns();
@@ -117,19 +121,31 @@ class SimDdBackend final : public DdBackend {
         __atomic_store_n(&ctl->exits, l.exits, __ATOMIC_RELEASE);
         break;
       }
-      l.head = want;
-      l.cur_seq = want;
-      l.cur_job = e.job_id;
-      l.cur_trailer = e.trailer;
-      // the job: a delay, then its trailer
+      uint32_t count = 1;
+      l.cur_job[0] = e.job_id;
+      l.cur_trailer[0] = e.trailer;
+      if (e.kind == setk::kDdKindScan)
+        for (; count < setk::kDdScanBatch; ++count) {
+          setk::DdEntry& f = ring[(l.head + count) & mask];
+          if (__atomic_load_n(&f.seq, __ATOMIC_ACQUIRE) != want + count || f.kind != setk::kDdKindScan) break;
+          l.cur_job[count] = f.job_id;
+          l.cur_trailer[count] = f.trailer;
+        }
+      l.head += count;
+      l.cur_first = want;
+      l.cur_count = count;
+      if (count > 1) g_batched_jobs.fetch_add(count);
+      // the jobs: a delay, then their trailers
       const long us = lo_ + (hi_ > lo_ ? (long)(l.rng() % (uint64_t)(hi_ - lo_ + 1)) : 0);
       if (us > 0) std::this_thread::sleep_for(std::chrono::microseconds(us));
-      const uint64_t k = jobs_.fetch_add(1) + 1;
-      set_trailer t;
-      t.job_id = (bad_every_ > 0 && k % (uint64_t)bad_every_ == 0) ? l.cur_job + 1000000007ull : l.cur_job;
-      t.slot_gen = lane;
-      t.word = (uint32_t)SET_TRAILER_MAGIC << 16;
-      std::memcpy(l.cur_trailer, &t, sizeof t);
+      for (uint32_t i = 0; i < count; ++i) {
+        const uint64_t k = jobs_.fetch_add(1) + 1;
+        set_trailer t;
+        t.job_id = (bad_every_ > 0 && k % (uint64_t)bad_every_ == 0) ? l.cur_job[i] + 1000000007ull : l.cur_job[i];
+        t.slot_gen = lane;
+        t.word = (uint32_t)SET_TRAILER_MAGIC << 16;
+        std::memcpy(l.cur_trailer[i], &t, sizeof t);
+      }
     }
     l.running.store(false, std::memory_order_release);
   }
@@ -151,3 +167,6 @@ class SimDdBackend final : public DdBackend {
 std::unique_ptr<DdBackend> make_dd_backend() { return std::make_unique<SimDdBackend>(); }
 
 }  // namespace setrt
+
+// Test probe: jobs the simulated loops have run in batches of two or more since the library loaded.
+extern "C" uint64_t set_sim_dd_batched_jobs() { return setrt::g_batched_jobs.load(); }

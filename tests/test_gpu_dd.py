@@ -270,3 +270,39 @@ def test_image_jobs_of_the_workload_sizes():
     for j in jobs:
         check_img(j)
     check_dd_trailers(jobs, 4)
+
+
+def test_queued_scan_jobs_batched_with_ragged_sizes_and_other_kinds():
+    # one lane with a deep ring: scan descriptors queue behind the running iteration and the fetch
+    # kernel takes up to kDdScanBatch consecutive ones at once (one launch of the scan node, one
+    # scratch area per job); blur and image jobs in between end a batch
+    from gpu_util import check_img, img_job
+    sizes = [65536, 1, 4097, 30001, 65535, 5, 4096, 8192, 100, 65536, 12289]
+    jobs = []
+    for k in range(300):
+        if k % 23 == 22:
+            jobs.append(blur_job(2000 + k, W=255, H=31, device=True))
+        elif k % 41 == 40:
+            jobs.append(img_job(2000 + k, dims=(129, 65), device=True))
+        else:
+            jobs.append(scan_job(2000 + k, n=sizes[k % len(sizes)], device=True))
+    st, _ = run_dd(jobs, num_lanes=1, ring_depth=64)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        {1: check_blur, 2: check_scan, 3: check_img}[j.type](j)
+    check_dd_trailers(jobs, 1)
+
+
+def test_bounded_wait_inside_a_batch_fails_only_its_job():
+    # the stalled job shares a scan-node launch with the jobs queued beside it; only it reports
+    # the bounded wait, the others (their own scratch areas) complete exactly
+    s = S()
+    jobs = [scan_job(2500 + k, n=65536, device=True) for k in range(12)]
+    jobs[5].desc.flags = s.SET_F_TEST_STALL
+    st, _ = run_dd(jobs, num_lanes=1, ring_depth=16)
+    assert st["completed"] == 12 and st["failed"] == 1 and st["canary_errors"] == 0, st
+    assert jobs[5].status.value == s.SET_EDEVICE
+    for k in range(12):
+        if k != 5:
+            assert jobs[k].status.value == s.SET_OK
+            check_scan(jobs[k])

@@ -214,3 +214,23 @@ def test_reset_stats_keeps_jobs_in_flight_counted(sim):
     st, _ = stats(sim, dd)
     assert sim.set_dd_destroy(dd) == B.SET_OK
     assert st.submitted == 100 and st.completed == 100 and st.jobs_per_s > 0 and st.p50_us > 0
+
+
+def test_queued_scan_jobs_retire_in_batches(sim):
+    # one lane, a deep ring and a slow simulated job: descriptors queue up behind the running one,
+    # so the loop takes several at once (up to the batch size) and retires them together with one
+    # jump of the done counter; every job still completes once with its own trailer
+    os.environ["SET_SIM_DD_DELAY_US"] = "200,400"
+    sim.set_sim_dd_batched_jobs.restype = ctypes.c_uint64
+    before = sim.set_sim_dd_batched_jobs()
+    jobs = Jobs(300)
+    dd = create(sim, num_lanes=1, ring_depth=32)
+    first = ctypes.c_uint64()
+    assert sim.set_dd_submit_many(dd, jobs.descs, jobs.n, ctypes.byref(first), None) == B.SET_OK
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert sim.set_dd_destroy(dd) == B.SET_OK
+    assert st.completed == jobs.n and st.failed == 0 and st.canary_errors == 0
+    for k in range(jobs.n):
+        assert jobs.trailer(k)[0] == first.value + k and jobs.status[k] == B.SET_OK
+    assert sim.set_sim_dd_batched_jobs() - before >= jobs.n // 2
