@@ -460,6 +460,10 @@ set_status set_dd_create(const set_dd_config* cfg, set_dd** out);
  * ring of the lane with the fewest jobs in flight (lowest index on ties) unless SET_F_NONBLOCK
  * (SET_EAGAIN), publishes the entry and relaunches the lane's graph if its loop has ended. */
 set_status set_dd_submit(set_dd* dd, const set_job_desc* job, uint64_t* job_id);
+/* As set_submit_many.  Consecutive jobs go to one lane in groups of up to 8 (one lane choice per
+ * group, the group published together, so queued scan jobs of a group run as one batch); a group
+ * ends before a job whose SET_F_NONBLOCK differs from its first job's, and a non-blocking group
+ * publishes what fits in the ring (SET_EAGAIN once nothing fits). */
 set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, uint64_t* first_id, size_t* n_done);
 
 /* As set_wait_all. */

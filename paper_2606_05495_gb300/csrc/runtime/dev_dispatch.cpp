@@ -7,7 +7,9 @@
 //
 // Submit plans the job's single stage kernel with the same planners as the executor, writes the
 // argument struct into the lane's next ring entry and publishes it with a release store of the
-// entry's sequence word.  Ring entries are reused only after the completion thread has handled
+// entry's sequence word; set_dd_submit_many does this for groups of up to kDdScanBatch
+// consecutive jobs on one lane (one lane choice and lock per group, sequence words stored last
+// entry first).  Ring entries are reused only after the completion thread has handled
 // the job that used them.  The completion thread reads each lane's done counter, completes the
 // jobs behind it (status from the completion word, latency) and relaunches lanes whose loop has
 // ended while descriptors are waiting; submitters relaunch too, under the lane's mutex.
@@ -59,7 +61,11 @@ class DevDispatch {
  public:
   ~DevDispatch() { release(); }
   set_status init(const set_dd_config& cfg, std::string* err);
-  set_status submit(const set_job_desc* d, uint64_t* id_out);
+  // Submits a group of up to min(n, kDdScanBatch, ring depth) jobs d[0..) to one lane: the prefix
+  // that validates; *n_done = jobs published (their ids *first_id, consecutive).  Returns the
+  // first job's error when no job was published, else the error of the job after the group (if
+  // one stopped it) or SET_OK.
+  set_status submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done);
   set_status wait_all(int64_t timeout_us);
   set_status stats(set_stats_t* out, uint64_t* launches);
   set_status reset_stats();
@@ -207,60 +213,89 @@ set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std:
   return SET_OK;
 }
 
-set_status DevDispatch::submit(const set_job_desc* d, uint64_t* id_out) {
+set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done) {
+  *n_done = 0;
   if (!d) return fail(SET_EINVAL, "null descriptor");
   if (stop_.load()) return SET_ESHUTDOWN;
   if (sticky_.load() != SET_OK) return (set_status)sticky_.load();
   const uint64_t t0 = now_ns();
-  setk::JobLayout L;
+  // the group: the prefix of d[0..n) that validates and shares d[0]'s SET_F_NONBLOCK, at most the
+  // ring's depth; a job that does not validate is reported after the jobs before it are published
+  n = std::min(n, std::min(depth_, setk::kDdScanBatch));
+  setk::JobLayout L[setk::kDdScanBatch];
+  uint32_t g = 0;
+  set_status bad = SET_OK;
   std::string why;
-  const set_status v = validate(*d, &L, &why);
-  if (v != SET_OK) return fail(v, why);
+  for (; g < n; ++g) {
+    if ((d[g].flags ^ d[0].flags) & SET_F_NONBLOCK) break;
+    bad = validate(d[g], &L[g], &why);
+    if (bad != SET_OK) break;
+  }
+  if (g == 0) return fail(bad, why);
 
   const uint32_t li = pick_lane();
   DdLane& l = *lanes_[li];
-  const uint64_t id = next_id_.fetch_add(1);
-  alignas(16) unsigned char args[setk::kDdArgBytes];
-  uint32_t args_size = 0;
-  if (!be_->plan(*d, id, li, args, &args_size))
-    return fail(SET_EINVAL, "set_dd: the job does not plan to one kernel with a small argument struct");
-
-  std::unique_lock<std::mutex> g(l.mu);
+  std::unique_lock<std::mutex> gl(l.mu);
   const uint64_t s = l.seq.load(std::memory_order_relaxed);
-  if (s - l.reaped.load(std::memory_order_acquire) >= depth_) {
-    if (d->flags & SET_F_NONBLOCK) return SET_EAGAIN;
-    ring_waits_.fetch_add(1, std::memory_order_relaxed);
-    const uint64_t limit = t0 + (uint64_t)cfg_.drain_timeout_ms * 1000000ull;
-    while (s - l.reaped.load(std::memory_order_acquire) >= depth_) {
-      maybe_relaunch_locked(li);
-      if (sticky_.load() != SET_OK) return (set_status)sticky_.load();
-      if (now_ns() > limit) return fail(SET_ETIMEDOUT, "set_dd_submit: the lane's ring stayed full");
-      std::this_thread::yield();
+  if (s + g - l.reaped.load(std::memory_order_acquire) > depth_) {
+    if (d[0].flags & SET_F_NONBLOCK) {  // publish what fits now
+      const uint64_t room = depth_ - (s - l.reaped.load(std::memory_order_acquire));
+      if (room == 0) return SET_EAGAIN;
+      g = (uint32_t)std::min<uint64_t>(g, room);
+      bad = SET_OK;
+    } else {
+      ring_waits_.fetch_add(1, std::memory_order_relaxed);
+      const uint64_t limit = t0 + (uint64_t)cfg_.drain_timeout_ms * 1000000ull;
+      while (s + g - l.reaped.load(std::memory_order_acquire) > depth_) {
+        maybe_relaunch_locked(li);
+        if (sticky_.load() != SET_OK) return (set_status)sticky_.load();
+        if (now_ns() > limit) return fail(SET_ETIMEDOUT, "set_dd_submit: the lane's ring stayed full");
+        std::this_thread::yield();
+      }
     }
   }
-  const uint32_t k = (uint32_t)(s & mask_);
-  DdInfo& inf = l.info[k];
-  inf.id = id;
-  inf.status = d->status;
-  inf.t_arrival = d->t_arrival_ns ? d->t_arrival_ns : t0;
-  setk::DdEntry& e = l.m.ring[k];
-  e.kind = d->type == SET_JOB_BLUR_HIST ? setk::kDdKindBlur
-           : d->type == SET_JOB_SAXPY_SCAN_MAX ? setk::kDdKindScan
-                                               : setk::kDdKindImg;
-  e.args_size = args_size;
-  e.job_id = id;
-  e.trailer = reinterpret_cast<set_trailer*>(static_cast<uint8_t*>(d->out) + L.out_bytes - sizeof(set_trailer));
-  std::memcpy(e.args, args, args_size);
-  __atomic_store_n(&e.seq, s + 1, __ATOMIC_RELEASE);
-  l.seq.store(s + 1, std::memory_order_release);
+  // ids and argument structs under the lane's lock, so that one submitter's ids stay consecutive
+  const uint64_t id0 = next_id_.fetch_add(g);
+  alignas(16) unsigned char args[setk::kDdScanBatch][setk::kDdArgBytes];
+  uint32_t args_size[setk::kDdScanBatch];
+  for (uint32_t k = 0; k < g; ++k)
+    if (!be_->plan(d[k], id0 + k, li, args[k], &args_size[k])) {
+      if (k == 0) return fail(SET_EINVAL, "set_dd: the job does not plan to one kernel with a small argument struct");
+      g = k;  // the ids after it are skipped
+      bad = SET_EINVAL;
+      why = "set_dd: the job does not plan to one kernel with a small argument struct";
+      break;
+    }
+  for (uint32_t k = 0; k < g; ++k) {
+    const uint32_t slot = (uint32_t)((s + k) & mask_);
+    DdInfo& inf = l.info[slot];
+    inf.id = id0 + k;
+    inf.status = d[k].status;
+    inf.t_arrival = d[k].t_arrival_ns ? d[k].t_arrival_ns : t0;
+    setk::DdEntry& e = l.m.ring[slot];
+    e.kind = d[k].type == SET_JOB_BLUR_HIST        ? setk::kDdKindBlur
+             : d[k].type == SET_JOB_SAXPY_SCAN_MAX ? setk::kDdKindScan
+                                                   : setk::kDdKindImg;
+    e.args_size = args_size[k];
+    e.job_id = id0 + k;
+    e.trailer = reinterpret_cast<set_trailer*>(static_cast<uint8_t*>(d[k].out) + L[k].out_bytes - sizeof(set_trailer));
+    std::memcpy(e.args, args[k], args_size[k]);
+  }
+  // Publish the group's sequence words last entry first: the lane's fetch waits on the first, and
+  // when it sees it the others are already complete, so queued scan jobs of one group run as one
+  // batch.
+  for (uint32_t k = g; k-- > 0;) __atomic_store_n(&l.m.ring[(s + k) & mask_].seq, s + k + 1, __ATOMIC_RELEASE);
+  l.seq.store(s + g, std::memory_order_release);
   uint64_t z = 0;
   t_first_.compare_exchange_strong(z, t0);
-  submitted_.fetch_add(1);
+  submitted_.fetch_add(g);
   maybe_relaunch_locked(li);
-  g.unlock();
+  gl.unlock();
   work_sig_.notify(1);
   submit_ns_.fetch_add(now_ns() - t0, std::memory_order_relaxed);
-  if (id_out) *id_out = id;
+  if (first_id) *first_id = id0;
+  *n_done = g;
+  if (bad != SET_OK) return fail(bad, why);
   return sticky_.load() == SET_OK ? SET_OK : (set_status)sticky_.load();
 }
 
@@ -485,18 +520,21 @@ set_status set_dd_create(const set_dd_config* cfg, set_dd** out) {
 
 set_status set_dd_submit(set_dd* dd, const set_job_desc* job, uint64_t* job_id) {
   if (!dd) return SET_EINVAL;
-  return dd->dd->submit(job, job_id);
+  uint32_t done = 0;
+  return dd->dd->submit(job, 1, job_id, &done);
 }
 
 set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, uint64_t* first_id, size_t* n_done) {
   if (!dd || (n && !jobs)) return SET_EINVAL;
   size_t k = 0;
   set_status st = SET_OK;
-  for (; k < n; ++k) {
+  while (k < n) {  // groups of consecutive jobs, one lane each
     uint64_t id = 0;
-    st = dd->dd->submit(&jobs[k], &id);
+    uint32_t done = 0;
+    st = dd->dd->submit(&jobs[k], (uint32_t)std::min<size_t>(n - k, setk::kDdScanBatch), &id, &done);
+    if (done && k == 0 && first_id) *first_id = id;
+    k += done;
     if (st != SET_OK) break;
-    if (k == 0 && first_id) *first_id = id;
   }
   if (n_done) *n_done = k;
   return st;

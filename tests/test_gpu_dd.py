@@ -125,7 +125,8 @@ def test_idle_lanes_end_their_loop_and_are_relaunched():
         launches = ctypes.c_uint64()
         st = s.set_stats_t()
         for wave in range(3):
-            batch = [scan_job(800 + 10 * wave + k, n=10000 + k, device=True) for k in range(6)]
+            # 12 jobs: set_dd_submit_many sends a group of 8 to one lane and the other 4 to the other
+            batch = [scan_job(800 + 20 * wave + k, n=10000 + k, device=True) for k in range(12)]
             arr = (s.set_job_desc * len(batch))(*[j.desc for j in batch])
             first = ctypes.c_uint64()
             s.dd_check(s.set_dd_submit_many(dd, arr, len(batch), ctypes.byref(first), None), "submit", dd)
@@ -135,7 +136,7 @@ def test_idle_lanes_end_their_loop_and_are_relaunched():
             jobs += batch
             time.sleep(0.05)  # far beyond idle_us: both loops end
         s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), ctypes.byref(launches)), "stats", dd)
-        assert st.completed == 18 and st.failed == 0
+        assert st.completed == 36 and st.failed == 0
         assert launches.value >= 6, launches.value  # each wave relaunched both lanes
     finally:
         assert s.set_dd_destroy(dd) == s.SET_OK
@@ -306,3 +307,40 @@ def test_bounded_wait_inside_a_batch_fails_only_its_job():
         if k != 5:
             assert jobs[k].status.value == s.SET_OK
             check_scan(jobs[k])
+
+
+def test_concurrent_submit_many_threads():
+    # four host threads each submit a share with set_dd_submit_many (groups of up to 8 jobs to one
+    # lane at a time, under the lanes' mutexes); ids are unique, every job's trailer carries its id
+    import threading
+    s = S()
+    jobs = [scan_job(3000 + k, n=(4096, 65000, 777, 20000)[k % 4] + k, device=True) for k in range(256)]
+    dd = s.dd_create(s.dd_default_config(num_lanes=5, ring_depth=16))
+    errs = []
+
+    def worker(t):
+        share = jobs[t * 64:(t + 1) * 64]
+        arr = (s.set_job_desc * len(share))(*[j.desc for j in share])
+        done = ctypes.c_size_t()
+        st = s.set_dd_submit_many(dd, arr, len(share), None, ctypes.byref(done))
+        if st != s.SET_OK or done.value != len(share):
+            errs.append((t, st, done.value))
+
+    try:
+        threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errs, errs
+        s.dd_check(s.set_dd_wait_all(dd, 120_000_000), "wait", dd)
+        st = s.set_stats_t()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
+        assert st.completed == len(jobs) and st.failed == 0 and st.canary_errors == 0
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+    for j in jobs:
+        j.id = j.trailer()[0]
+        check_scan(j)
+    assert len({j.id for j in jobs}) == len(jobs)
+    check_dd_trailers(jobs, 5)

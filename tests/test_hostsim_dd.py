@@ -96,7 +96,7 @@ def test_every_job_completes_once_with_its_trailer(sim):
         jid, lane, word = jobs.trailer(k)
         assert jid == first.value + k and word == B.SET_TRAILER_MAGIC << 16 and jobs.status[k] == B.SET_OK
         lanes.add(lane)
-    assert lanes == set(range(5))  # the shortest-lane choice spreads the jobs
+    assert lanes == set(range(5))  # the shortest-lane choice spreads the groups of jobs
     assert launches >= 5
 
 
@@ -135,7 +135,9 @@ def test_idle_loops_end_and_are_relaunched(sim):
         time.sleep(0.02)  # far beyond idle_us: every loop ends
     st, launches = stats(sim, dd)
     assert sim.set_dd_destroy(dd) == B.SET_OK
-    assert st.completed == 60 and launches >= 4 * 3
+    # set_dd_submit_many sends groups of up to 8 consecutive jobs to one lane: 15 jobs reach two
+    # lanes per wave, whose loops ended during the previous wave's idle time
+    assert st.completed == 60 and launches >= 4 * 2
 
 
 def test_full_ring_nonblocking_and_blocking(sim):
@@ -234,3 +236,38 @@ def test_queued_scan_jobs_retire_in_batches(sim):
     for k in range(jobs.n):
         assert jobs.trailer(k)[0] == first.value + k and jobs.status[k] == B.SET_OK
     assert sim.set_sim_dd_batched_jobs() - before >= jobs.n // 2
+
+
+def test_submit_many_stops_at_an_invalid_job(sim):
+    # the jobs before the invalid one are published (in groups) and complete with consecutive ids;
+    # n_done is the invalid job's index and nothing after it is submitted
+    jobs = Jobs(20)
+    jobs.descs[13].in_bytes += 4
+    dd = create(sim, num_lanes=2, ring_depth=16)
+    first, done = ctypes.c_uint64(), ctypes.c_size_t()
+    assert sim.set_dd_submit_many(dd, jobs.descs, jobs.n, ctypes.byref(first), ctypes.byref(done)) == B.SET_EINVAL
+    assert done.value == 13 and b"in_bytes" in sim.set_dd_last_error(dd)
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert sim.set_dd_destroy(dd) == B.SET_OK
+    assert st.submitted == st.completed == 13 and st.failed == 0
+    for k in range(13):
+        assert jobs.trailer(k)[0] == first.value + k and jobs.status[k] == B.SET_OK
+    assert all(jobs.status[k] == 99 for k in range(13, 20))
+
+
+def test_submit_many_nonblocking_publishes_what_fits(sim):
+    os.environ["SET_SIM_DD_DELAY_US"] = "30000,30000"  # the first job holds the lane for 30 ms
+    jobs = Jobs(10)
+    for k in range(jobs.n):
+        jobs.descs[k].flags = B.SET_F_NONBLOCK
+    dd = create(sim, num_lanes=1, ring_depth=4)
+    first, done = ctypes.c_uint64(), ctypes.c_size_t()
+    assert sim.set_dd_submit_many(dd, jobs.descs, jobs.n, ctypes.byref(first), ctypes.byref(done)) == B.SET_EAGAIN
+    assert done.value == 4
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert sim.set_dd_destroy(dd) == B.SET_OK
+    assert st.submitted == st.completed == 4 and st.failed == 0
+    for k in range(4):
+        assert jobs.trailer(k)[0] == first.value + k and jobs.status[k] == B.SET_OK
