@@ -69,8 +69,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--lanes", type=int, default=16, help="device-dispatch arm (set_dd): lanes")
-    p.add_argument("--dd-arm", action="store_true", help="add the device-dispatch arm (set_dd) to the scan line")
+    p.add_argument("--lanes", type=int, default=32, help="device-dispatch arm (set_dd): lanes")
+    p.add_argument("--no-dd-arm", dest="dd_arm", action="store_false",
+                   help="leave out the device-dispatch arm (set_dd) of the scan line")
     p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates",
                                           "dd-study"],
                    default="scan",
@@ -421,13 +422,20 @@ def device_dispatch_arm(S, w: "Workload", lanes: int, dev_index: int, args, d: D
     finally:
         S.set_dd_destroy(dd)
     world = d.world
+    alg = 16 * N_ELEM + 32  # per job: read x, y; write z, S; m + trailer
+    gbs = nj * alg / (ms_d * 1e-3) / 1e9
+    peak = _peaks().get("hbm_gbs", 6800.0)
     return {
         "value": world * nj / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "lanes": lanes,
         "submit_threads": threads,
         "p50_us": st_d["p50_us"], "p99_us": st_d["p99_us"], "submit_us": st_d["mean_launch_us"],
         "graph_launches": launches, "failed": st_d["failed"], "canary_errors": st_d["canary_errors"],
-        "note": "set_dd: per lane one graph WHILE {fetch -> SWITCH {scan}} looping on the device; the host "
-                "writes one descriptor per job (no graph update, launch or callback per job)",
+        "hbm": {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "alg_bytes_per_job": alg,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "note": "set_dd: per lane one graph WHILE {fetch -> SWITCH {blur | scan | image}} looping on the device; "
+                "the host writes one descriptor per job (no graph update, launch or callback per job); "
+                "set_dd_submit_many groups up to 8 jobs per lane and a lane runs up to 8 queued scan jobs "
+                "in one launch",
     }
 
 

@@ -27,6 +27,26 @@ struct DdLaneMem {
   void* img_state = nullptr;      // the image kernel's ticket and histogram accumulator (device memory)
 };
 
+// Device allocations a backend has already accepted during one submit call ([lo, hi) ranges), so
+// that jobs carved out of the same allocations are not checked with the driver again.  Lives no
+// longer than the call: memory freed and mapped again later is checked afresh.
+struct DdRangeCache {
+  static constexpr int kN = 4;
+  uintptr_t lo[kN] = {}, hi[kN] = {};
+  int n = 0, next = 0;
+  bool has(uintptr_t p, size_t bytes) const {
+    for (int i = 0; i < n; ++i)
+      if (p >= lo[i] && p <= hi[i] && bytes <= hi[i] - p) return true;
+    return false;
+  }
+  void add(uintptr_t a, uintptr_t b) {
+    lo[next] = a;
+    hi[next] = b;
+    next = (next + 1) % kN;
+    if (n < kN) ++n;
+  }
+};
+
 class DdBackend {
  public:
   virtual ~DdBackend() = default;
@@ -36,8 +56,9 @@ class DdBackend {
   // The job's kernel argument struct (<= kDdArgBytes) over the lane's kernel state.
   virtual bool plan(const set_job_desc& d, uint64_t job_id, uint32_t lane, unsigned char* args,
                     uint32_t* args_size) = 0;
-  // True if the lanes' kernels may use p as a job buffer in place.
-  virtual bool buffer_ok(const void* p) const = 0;
+  // True if the lanes' kernels may use [p, p + bytes) as a job buffer in place.  cache (may be
+  // null): allocations accepted earlier in the same submit call.
+  virtual bool buffer_ok(const void* p, size_t bytes, DdRangeCache* cache) const = 0;
   // Launches the lane's loop, ordered after its previous launch.
   virtual set_status launch(uint32_t lane, std::string* err) = 0;
   // 1: every launch of the lane has completed; 0: one is still running; -1: the lane failed (err).

@@ -45,6 +45,15 @@ class CudaDdBackend final : public DdBackend {
     DD_CK(cudaSetDevice(cfg.device));
     DD_CK(cudaFree(nullptr));
     DD_CK(setk::kernels_init());
+    {
+      void* fp = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fp, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+          q == cudaDriverEntryPointSuccess)
+        range_fn_ = reinterpret_cast<int (*)(unsigned long long*, size_t*, unsigned long long)>(fp);
+      else
+        cudaGetLastError();
+    }
     const uint32_t nl = (uint32_t)cfg.num_lanes;
     const size_t ring_bytes = (size_t)depth * sizeof(setk::DdEntry);
     const size_t cmpl_bytes = setk::align256((size_t)depth * sizeof(uint32_t));
@@ -127,13 +136,23 @@ class CudaDdBackend final : public DdBackend {
   }
 
   // device memory of the backend's GPU (the lanes' kernels read and write the buffers in place)
-  bool buffer_ok(const void* p) const override {
+  // Device memory of the object's GPU; where the driver reports the allocation's range, the whole
+  // buffer must lie inside it, and the range is remembered for the rest of the submit call.
+  bool buffer_ok(const void* p, size_t bytes, DdRangeCache* cache) const override {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (cache && cache->has(a, bytes)) return true;
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    return at.type == cudaMemoryTypeDevice && at.device == cfg_.device;
+    if (at.type != cudaMemoryTypeDevice || at.device != cfg_.device) return false;
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (!range_fn_ || range_fn_(&base, &size, (unsigned long long)a) != 0) return true;  // start checked only
+    if (a < base || bytes > base + size - a) return false;  // runs past the end of its allocation
+    if (cache) cache->add((uintptr_t)base, (uintptr_t)(base + size));
+    return true;
   }
 
   set_status launch(uint32_t lane, std::string* err) override {
@@ -275,6 +294,8 @@ class CudaDdBackend final : public DdBackend {
   void* host_block_ = nullptr;
   void* dev_block_ = nullptr;
   size_t scan_stride_ = 0;  // bytes between the scan look-back areas of one lane
+  // the driver's cuMemGetAddressRange (base, size of the allocation holding an address; 0 = found)
+  int (*range_fn_)(unsigned long long*, size_t*, unsigned long long) = nullptr;
   bool leaked_ = false;
 };
 

@@ -65,7 +65,7 @@ class DevDispatch {
   // that validates; *n_done = jobs published (their ids *first_id, consecutive).  Returns the
   // first job's error when no job was published, else the error of the job after the group (if
   // one stopped it) or SET_OK.
-  set_status submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done);
+  set_status submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done, DdRangeCache* cache);
   set_status wait_all(int64_t timeout_us);
   set_status stats(set_stats_t* out, uint64_t* launches);
   set_status reset_stats();
@@ -88,7 +88,7 @@ class DevDispatch {
   set_status launch_locked(uint32_t i);
   bool maybe_relaunch_locked(uint32_t i);
   uint32_t pick_lane();
-  set_status validate(const set_job_desc& d, setk::JobLayout* L, std::string* why) const;
+  set_status validate(const set_job_desc& d, setk::JobLayout* L, std::string* why, DdRangeCache* cache) const;
   void poll_main();
   void reap(DdLane& l, uint64_t upto);
   void release();
@@ -181,7 +181,8 @@ uint32_t DevDispatch::pick_lane() {
   return best;
 }
 
-set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std::string* why) const {
+set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std::string* why,
+                                 DdRangeCache* cache) const {
   if (d.type != SET_JOB_BLUR_HIST && d.type != SET_JOB_SAXPY_SCAN_MAX && d.type != SET_JOB_IMG_SOBEL_HIST) {
     *why = "set_dd: only SET_JOB_BLUR_HIST, SET_JOB_SAXPY_SCAN_MAX and SET_JOB_IMG_SOBEL_HIST jobs";
     return SET_EINVAL;
@@ -202,8 +203,8 @@ set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std:
     *why = "null in/out, or in_bytes/out_bytes do not match the job type's layout";
     return SET_EINVAL;
   }
-  if (!be_->buffer_ok(d.in) || !be_->buffer_ok(d.out)) {
-    *why = "set_dd: in/out must be device memory of the object's GPU";
+  if (!be_->buffer_ok(d.in, d.in_bytes, cache) || !be_->buffer_ok(d.out, d.out_bytes, cache)) {
+    *why = "set_dd: in/out must be device memory of the object's GPU, each inside one allocation";
     return SET_EINVAL;
   }
   if (((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u) != 0) {
@@ -213,7 +214,8 @@ set_status DevDispatch::validate(const set_job_desc& d, setk::JobLayout* L, std:
   return SET_OK;
 }
 
-set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done) {
+set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* first_id, uint32_t* n_done,
+                               DdRangeCache* cache) {
   *n_done = 0;
   if (!d) return fail(SET_EINVAL, "null descriptor");
   if (stop_.load()) return SET_ESHUTDOWN;
@@ -228,7 +230,7 @@ set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* firs
   std::string why;
   for (; g < n; ++g) {
     if ((d[g].flags ^ d[0].flags) & SET_F_NONBLOCK) break;
-    bad = validate(d[g], &L[g], &why);
+    bad = validate(d[g], &L[g], &why, cache);
     if (bad != SET_OK) break;
   }
   if (g == 0) return fail(bad, why);
@@ -521,17 +523,19 @@ set_status set_dd_create(const set_dd_config* cfg, set_dd** out) {
 set_status set_dd_submit(set_dd* dd, const set_job_desc* job, uint64_t* job_id) {
   if (!dd) return SET_EINVAL;
   uint32_t done = 0;
-  return dd->dd->submit(job, 1, job_id, &done);
+  setrt::DdRangeCache cache;
+  return dd->dd->submit(job, 1, job_id, &done, &cache);
 }
 
 set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, uint64_t* first_id, size_t* n_done) {
   if (!dd || (n && !jobs)) return SET_EINVAL;
   size_t k = 0;
   set_status st = SET_OK;
+  setrt::DdRangeCache cache;  // buffers of this call's jobs usually share a few allocations
   while (k < n) {  // groups of consecutive jobs, one lane each
     uint64_t id = 0;
     uint32_t done = 0;
-    st = dd->dd->submit(&jobs[k], (uint32_t)std::min<size_t>(n - k, setk::kDdScanBatch), &id, &done);
+    st = dd->dd->submit(&jobs[k], (uint32_t)std::min<size_t>(n - k, setk::kDdScanBatch), &id, &done, &cache);
     if (done && k == 0 && first_id) *first_id = id;
     k += done;
     if (st != SET_OK) break;

@@ -70,7 +70,7 @@ class SimDdBackend final : public DdBackend {
     *args_size = 0;  // the simulated loop needs only the entry's job id and trailer
     return true;
   }
-  bool buffer_ok(const void* p) const override { return p != nullptr; }
+  bool buffer_ok(const void* p, size_t, DdRangeCache*) const override { return p != nullptr; }
 
   set_status launch(uint32_t lane, std::string*) override {
     SimLane& l = *lanes_[lane];

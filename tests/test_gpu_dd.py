@@ -344,3 +344,47 @@ def test_concurrent_submit_many_threads():
         check_scan(j)
     assert len({j.id for j in jobs}) == len(jobs)
     check_dd_trailers(jobs, 5)
+
+
+def test_buffer_running_past_its_allocation_is_refused():
+    # the driver reports the allocation that holds a buffer's start; a buffer whose extent runs
+    # past its end is refused at submit (nothing is published).  The allocation is a caching-
+    # allocator segment of its own, and the test first asks the driver for its range itself, so
+    # that it submits only when the refusal is certain.
+    t = __import__("torch")
+    s = S()
+    t.cuda.empty_cache()
+    seg = 20 << 20
+    buf = t.empty(seg, dtype=t.uint8, device="cuda")
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError:
+        pytest.skip("driver library not loadable by name")
+    base, size = ctypes.c_uint64(), ctypes.c_size_t()
+    if cu.cuMemGetAddressRange_v2(ctypes.byref(base), ctypes.byref(size), ctypes.c_uint64(buf.data_ptr())) != 0:
+        pytest.skip("the driver reports no allocation range here")
+    end = base.value + size.value
+    assert base.value <= buf.data_ptr() < end
+    n = 1000
+    out_bytes = s.set_job_out_bytes(s.SET_JOB_SAXPY_SCAN_MAX, s.dims4(n))
+    good = scan_job(3500, n=n, device=True)
+    past = (end - 4096) & ~15  # 16-byte aligned, fewer than out_bytes left before the end
+    assert end - past < out_bytes
+    d = s.make_desc(s.SET_JOB_SAXPY_SCAN_MAX, (n,), good.hin.data_ptr(), past)
+    dd = s.dd_create(s.dd_default_config(num_lanes=1))
+    try:
+        assert s.set_dd_submit(dd, ctypes.byref(d), None) == s.SET_EINVAL
+        assert b"inside one allocation" in s.set_dd_last_error(dd)
+        st = s.set_stats_t()
+        s.dd_check(s.set_dd_stats(dd, ctypes.byref(st), None), "stats", dd)
+        assert st.submitted == 0
+        # the same job with its own output is accepted and runs
+        jid = ctypes.c_uint64()
+        s.dd_check(s.set_dd_submit(dd, ctypes.byref(good.desc), ctypes.byref(jid)), "submit", dd)
+        good.id = jid.value
+        s.dd_check(s.set_dd_wait_all(dd, 60_000_000), "wait", dd)
+    finally:
+        assert s.set_dd_destroy(dd) == s.SET_OK
+    del buf
+    check_scan(good)
+    check_dd_trailers([good], 1)
