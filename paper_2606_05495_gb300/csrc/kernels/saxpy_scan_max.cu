@@ -78,11 +78,11 @@ __device__ __forceinline__ uint64_t max_word(uint32_t epoch, float m) {
 
 // One tile of the job (the whole kernel body): shared by the kernel that takes its arguments by
 // value and the device-dispatch lane kernel that reads them from device memory.
-__device__ __forceinline__ void scan_tile(const ScanArgs& p, const uint32_t tile) {
+__device__ __forceinline__ void scan_tile(const ScanArgs& p, uint8_t* const scratch, const uint32_t tile) {
   __shared__ float s_wsum[kWarps], s_wexcl[kWarps], s_wmax[kWarps];
   __shared__ float s_prefix;
-  ScanHdr* hdr = reinterpret_cast<ScanHdr*>(p.scratch);
-  uint64_t* status = reinterpret_cast<uint64_t*>(p.scratch + sizeof(ScanHdr));
+  ScanHdr* hdr = reinterpret_cast<ScanHdr*>(scratch);
+  uint64_t* status = reinterpret_cast<uint64_t*>(scratch + sizeof(ScanHdr));
   uint64_t* maxw = status + p.T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -278,7 +278,7 @@ __device__ __forceinline__ void scan_tile(const ScanArgs& p, const uint32_t tile
 }
 
 __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_constant__ ScanArgs p) {
-  scan_tile(p, blockIdx.x);
+  scan_tile(p, p.scratch, blockIdx.x);
 }
 
 // Device-dispatch lane kernel: the graph node's grid is fixed, kDdScanBatch groups of tmax blocks
@@ -286,13 +286,13 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_c
 // the `*count` scan jobs of this iteration into consecutive kDdArgBytes areas of device memory;
 // group j runs job j (block j * tmax + t is its tile t) on scratch area j (the planned scratch +
 // j * scratch_stride), and blocks past a job's tile count, or of groups past `*count`, leave at once.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
     saxpy_scan_max_lane_kernel(const unsigned char* __restrict__ args, const uint32_t* __restrict__ count,
                                uint32_t tmax, uint64_t scratch_stride) {
   const uint32_t j = blockIdx.x / tmax, tile = blockIdx.x - j * tmax;
   if (j >= *count || j >= kDdScanBatch) return;
-  ScanArgs p = *reinterpret_cast<const ScanArgs*>(args + (size_t)j * kDdArgBytes);
-  p.scratch += (size_t)j * scratch_stride;
+  const ScanArgs& p = *reinterpret_cast<const ScanArgs*>(args + (size_t)j * kDdArgBytes);
+  uint8_t* const scratch = p.scratch + (size_t)j * scratch_stride;
   const uint32_t T = p.T, n = p.n;
   if (tile >= T) return;
   // arguments that do not describe a job this node can run (a tile count beyond the group, n out
@@ -302,13 +302,13 @@ __global__ void __launch_bounds__(kThreads)
   // kernel's 16-byte accesses to them are taken only when n is a multiple of 4; the trailer
   // follows 8n + 16 bytes of output, so it is 8-byte aligned)
   const uintptr_t al16 = reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.z) |
-                         reinterpret_cast<uintptr_t>(p.scratch);
+                         reinterpret_cast<uintptr_t>(scratch);
   const uintptr_t al4 = reinterpret_cast<uintptr_t>(p.y) | reinterpret_cast<uintptr_t>(p.S) |
                         reinterpret_cast<uintptr_t>(p.m_out);
   if (T > tmax || n == 0 || n > T * kTile || n <= (T - 1) * kTile || (al16 & 15u) != 0 || (al4 & 3u) != 0 ||
       (reinterpret_cast<uintptr_t>(p.trailer) & 7u) != 0)
     return;
-  scan_tile(p, tile);
+  scan_tile(p, scratch, tile);
 }
 
 static_assert(sizeof(ScanArgs) <= kDdArgBytes, "a scan job's arguments fit one lane argument area");
