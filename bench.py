@@ -1015,6 +1015,22 @@ def run_workload(args, d: Dist):
         line["roofline"] = _roofline_hbm("blur_hist_kernel", 2 * 65536 + 1040, statistics.mean(ts))
         # kernels reading and writing the pinned buffers over NVLink-C2C, no copy nodes
         line["set_mapped_io"] = _rate(S, dict(polled, io_mode=S.SET_IO_MAPPED), js.descs, n, args, d)
+        if not _profiler_attached():
+            # HBM-resident blur jobs: the executor (in place) against the device-dispatch lanes, which
+            # run queued blur jobs in batches of up to 8 clusters per launch
+            alg = 2 * 65536 + 1040
+            line["hbm_resident"] = {"jobs": n, "alg_bytes_per_job": alg, "executor_inplace": _rate(
+                S, dict(polled, io_mode=S.SET_IO_DEVICE_INPLACE, num_workers=4, num_streams=8), js.descs_dev, n,
+                args, d)}
+            ddb = S.dd_create(S.dd_default_config(num_lanes=32, device=d.local))
+            try:
+                ms_dd, st_dd, _ = timed_dd(S, ddb, js.descs_dev, n, args, d)
+            finally:
+                S.set_dd_destroy(ddb)
+            rate = n / (ms_dd * 1e-3)
+            line["hbm_resident"]["set_dd_32_lanes"] = {
+                "jobs_per_s": rate, "p50_us": st_dd["p50_us"], "p99_us": st_dd["p99_us"], "failed": st_dd["failed"],
+                "hbm_frac": rate * alg / 1e9 / _peaks().get("hbm_gbs", 6800.0)}
     elif args.workload in ("img", "mlp"):
         kind = 3 if args.workload == "img" else 4
         n = min(args.jobs, 2000)

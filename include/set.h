@@ -421,9 +421,9 @@ set_status set_serve(set_ctx* ctx, int mode, const set_job_desc* jobs, const uin
  * iteration retires the jobs the previous iteration ran (a completion word each and a counter
  * written to host memory, which a thread of the context reads to complete the jobs), waits a
  * bounded time for the next descriptor, copies its arguments into the lane's device memory and
- * selects the SWITCH body.  A scan descriptor takes with it the scan descriptors queued directly
- * behind it (up to 8, those already published): the scan node runs them in one launch, each on a
- * scratch area of its own.  Per job the host writes one descriptor: no graph update, no graph
+ * selects the SWITCH body.  A blur or scan descriptor takes with it the descriptors of the same
+ * kind queued directly behind it (up to 8, those already published): the node runs them in one
+ * launch (a cluster per blur job; a group of tiles and a scratch area per scan job).  Per job the host writes one descriptor: no graph update, no graph
  * launch and no host callback.  A lane whose fetch sees no descriptor for idle_us ends its loop; the host
  * relaunches the lane's graph when work arrives.  The paper's executor (set_create) keeps the host
  * in the loop; this variant measures the device-side alternative.
@@ -461,9 +461,9 @@ set_status set_dd_create(const set_dd_config* cfg, set_dd** out);
  * (SET_EAGAIN), publishes the entry and relaunches the lane's graph if its loop has ended. */
 set_status set_dd_submit(set_dd* dd, const set_job_desc* job, uint64_t* job_id);
 /* As set_submit_many.  Consecutive jobs go to one lane in groups of up to 8 (one lane choice per
- * group, the group published together, so queued scan jobs of a group run as one batch); a group
- * ends before a job whose SET_F_NONBLOCK differs from its first job's, and a non-blocking group
- * publishes what fits in the ring (SET_EAGAIN once nothing fits). */
+ * group, the group published together, so the group's queued blur or scan jobs run as one batch);
+ * a group ends before a job whose SET_F_NONBLOCK differs from its first job's, and a non-blocking
+ * group publishes what fits in the ring (SET_EAGAIN once nothing fits). */
 set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, uint64_t* first_id, size_t* n_done);
 
 /* As set_wait_all. */

@@ -9,6 +9,7 @@
 #include <cooperative_groups.h>
 
 #include "cp_async.cuh"
+#include "dev_dispatch.h"
 #include "stages.h"
 
 namespace cg = cooperative_groups;
@@ -136,10 +137,16 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
   blur_hist_body(a);
 }
 
-// Device-dispatch lane kernel: arguments of the job in flight in device memory (written by the
-// lane's fetch kernel); the node's dynamic shared memory covers the lane's widest image.
+// Device-dispatch lane kernel: the node's grid is kDdBatch clusters; the lane's fetch kernel
+// writes the arguments of the `*count` blur jobs of this iteration into consecutive kDdArgBytes
+// areas of device memory, cluster j runs job j and clusters past `*count` leave at once (all CTAs
+// of a cluster take the same decision, so no cluster barrier is left waiting).  The node's
+// dynamic shared memory covers the lane's widest image.
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
-    blur_hist_lane_kernel(const BlurHistArgs* __restrict__ pa) {
+    blur_hist_lane_kernel(const unsigned char* __restrict__ args, const uint32_t* __restrict__ count) {
+  const uint32_t j = blockIdx.x / kCluster;
+  if (j >= *count || j >= kDdBatch) return;
+  const BlurHistArgs* pa = reinterpret_cast<const BlurHistArgs*>(args + (size_t)j * kDdArgBytes);
   // arguments that do not describe a job this node can run (an empty or too wide image for the
   // node's shared memory, null or unaligned buffers) run nothing: every CTA of the cluster takes
   // the same decision, the trailer stays unwritten and the fetch kernel reports it
@@ -152,6 +159,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads)
     return;
   blur_hist_body(*pa);
 }
+
+static_assert(sizeof(BlurHistArgs) <= kDdArgBytes, "a blur job's arguments fit one lane argument area");
 
 inline unsigned blur_smem(uint32_t W) { return (unsigned)((kChunkRows + 2) * ((W + 15) & ~15u)); }
 

@@ -119,25 +119,26 @@ __global__ void __launch_bounds__(32) dd_fetch_kernel(const __grid_constant__ Dd
     return;
   }
 
-  // Peek at the kind, then take the entry into the argument area of its node.  A scan job also
-  // takes the scan descriptors that directly follow it and are already complete (up to
-  // kDdScanBatch): they run in the same launch of the scan node.
+  // Peek at the kind, then take the entry into the argument area of its node.  A blur or scan job
+  // also takes the descriptors of the same kind that directly follow it and are already complete
+  // (up to kDdBatch): they run in the same launch of the node.
   uint64_t job = 0, tr = 0;
   const uint32_t kind = (uint32_t)__shfl_sync(kFull, ld_relaxed_sys(reinterpret_cast<const uint64_t*>(e) + 1), 0);
+  const bool batched = kind == kDdKindScan || kind == kDdKindBlur;
   uint32_t count = 1;
-  if (kind == kDdKindScan) {
-    take_entry(e, L->scan_args[0], lane, &job, &tr);
+  if (batched) {
+    take_entry(e, L->batch_args[0], lane, &job, &tr);
     if (lane == 0) {
       L->cur_job[0] = job;
       L->cur_trailer[0] = reinterpret_cast<set_trailer*>(tr);
     }
-    for (; count < kDdScanBatch; ++count) {
+    for (; count < kDdBatch; ++count) {
       const DdEntry* f = a.ring + ((head + count) & mask);
       const uint64_t s = ld_acquire_sys(&f->seq);
       if (!__all_sync(kFull, s == want + count)) break;
       const uint64_t k = ld_relaxed_sys(reinterpret_cast<const uint64_t*>(f) + 1);
-      if ((uint32_t)__shfl_sync(kFull, k, 0) != kDdKindScan) break;
-      take_entry(f, L->scan_args[count], lane, &job, &tr);
+      if ((uint32_t)__shfl_sync(kFull, k, 0) != kind) break;
+      take_entry(f, L->batch_args[count], lane, &job, &tr);
       if (lane == 0) {
         L->cur_job[count] = job;
         L->cur_trailer[count] = reinterpret_cast<set_trailer*>(tr);
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(32) dd_fetch_kernel(const __grid_constant__ Dd
     L->cur_trailer[0] = nullptr;
   }
   if (lane == 0) {
-    L->scan_count = kind == kDdKindScan ? count : 0u;
+    L->batch_count = batched ? count : 0u;
     L->head = head + count;
     L->cur_first = want;
     L->cur_count = count;

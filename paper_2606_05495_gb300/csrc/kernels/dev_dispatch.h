@@ -4,9 +4,9 @@
 // A lane is one stream running one graph: WHILE { fetch -> SWITCH(kind) { blur | scan | image } }.
 // The host writes job descriptors into the lane's ring (page-locked host memory the GPU reads
 // over the host link); the fetch kernel of each iteration retires the job the previous iteration
-// ran (completion word and counter into host memory), waits a bounded time for the next
-// descriptor, copies its kernel arguments into the lane's device block and selects the kind for
-// the SWITCH node.  No descriptor within the idle limit: it ends the loop and counts an exit.
+// ran (completion words and counter into host memory), waits a bounded time for the next
+// descriptor, copies its kernel arguments (and those of the same-kind descriptors queued behind
+// it, up to kDdBatch) into the lane's device block and selects the kind for the SWITCH node.  No descriptor within the idle limit: it ends the loop and counts an exit.
 #pragma once
 
 #include <cstddef>
@@ -19,10 +19,12 @@ namespace setk {
 constexpr uint32_t kDdKindBlur = 0, kDdKindScan = 1, kDdKindImg = 2, kDdKinds = 3;
 constexpr uint32_t kDdKindNone = 7;  // >= the SWITCH node's body count: no body runs
 constexpr size_t kDdArgBytes = 192;
-// Scan jobs one loop iteration may take at once: consecutive scan descriptors already waiting in
-// the ring run as one launch of the scan node (a block of the lane's grid per tile of each job).
-// The job at sequence s uses the lane's scan scratch s % kDdScanBatch.
-constexpr uint32_t kDdScanBatch = 8;
+// Jobs one loop iteration may take at once: consecutive blur or scan descriptors of the same kind
+// already waiting in the ring run as one launch of their node (job j of the batch on the j-th
+// group of the node's grid: a cluster of the blur node, a tile range of the scan node with its
+// own look-back scratch).  Image jobs run one per iteration (their node's grid pulls the tiles of
+// one image from the lane's ticket).
+constexpr uint32_t kDdBatch = 8;
 
 // One ring entry: 32 8-byte words, read by the fetch kernel's warp with one word per thread.
 // The host fills words 1..31, then stores seq (word 0) with release order.
@@ -52,13 +54,13 @@ struct alignas(64) DdLaneDev {
   uint64_t cur_first;  // sequence + 1 of the first job in flight (0: none to retire)
   uint32_t cur_count;  // jobs in flight (consecutive sequences)
   uint32_t exits;      // loop exits so far (mirrors DdCtl::exits)
-  uint32_t scan_count; // scan jobs the scan node runs this iteration (read by the scan kernel)
+  uint32_t batch_count; // jobs in batch_args this iteration (read by the blur or scan kernel)
   uint32_t pad0;
   uint64_t pad1[4];
-  uint64_t cur_job[kDdScanBatch];              // job ids in flight
-  set_trailer* cur_trailer[kDdScanBatch];      // their trailers
-  alignas(64) unsigned char args[kDdKinds][kDdArgBytes];  // blur and image node arguments
-  alignas(64) unsigned char scan_args[kDdScanBatch][kDdArgBytes];  // the scan jobs of the batch
+  uint64_t cur_job[kDdBatch];          // job ids in flight
+  set_trailer* cur_trailer[kDdBatch];  // their trailers
+  alignas(64) unsigned char args[kDdKinds][kDdArgBytes];        // a kind that runs one job (image)
+  alignas(64) unsigned char batch_args[kDdBatch][kDdArgBytes];  // the blur or scan jobs of the batch
 };
 
 struct DdFetchArgs {

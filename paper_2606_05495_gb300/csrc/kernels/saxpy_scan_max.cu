@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) saxpy_scan_max_kernel(const __grid_c
   scan_tile(p, p.scratch, blockIdx.x);
 }
 
-// Device-dispatch lane kernel: the graph node's grid is fixed, kDdScanBatch groups of tmax blocks
+// Device-dispatch lane kernel: the graph node's grid is fixed, kDdBatch groups of tmax blocks
 // (tmax = the tiles of the lane's largest job).  The lane's fetch kernel writes the arguments of
 // the `*count` scan jobs of this iteration into consecutive kDdArgBytes areas of device memory;
 // group j runs job j (block j * tmax + t is its tile t) on scratch area j (the planned scratch +
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     saxpy_scan_max_lane_kernel(const unsigned char* __restrict__ args, const uint32_t* __restrict__ count,
                                uint32_t tmax, uint64_t scratch_stride) {
   const uint32_t j = blockIdx.x / tmax, tile = blockIdx.x - j * tmax;
-  if (j >= *count || j >= kDdScanBatch) return;
+  if (j >= *count || j >= kDdBatch) return;
   const ScanArgs& p = *reinterpret_cast<const ScanArgs*>(args + (size_t)j * kDdArgBytes);
   uint8_t* const scratch = p.scratch + (size_t)j * scratch_stride;
   const uint32_t T = p.T, n = p.n;

@@ -106,11 +106,12 @@ bool plan_mlp_batch(const BatchItem* items, int nb, const BatchLayout& L, uint8_
 // the slot at slot_base (plant: the SET_F_TEST_GUARD hook).
 void plan_guards(uint8_t* slot_base, const JobLayout& L, bool plant, KernelLaunch* arm, KernelLaunch* check);
 
-// Device-dispatch lane kernels and their fixed launch shapes.  The blur and image kernels take one
-// argument: a pointer to the job's argument struct in device memory.  The scan kernel takes
-// (argument areas of kDdArgBytes each, pointer to the number of jobs, tmax, scratch stride) and
-// runs on a grid of kDdScanBatch * tmax blocks, tmax = scan_lane_tiles(the lane's largest n).  The
-// blur node's dynamic shared memory covers its widest image.
+// Device-dispatch lane kernels and their fixed launch shapes.  The blur kernel takes (argument
+// areas of kDdArgBytes each, pointer to the number of jobs) and runs on kDdBatch clusters of 8
+// CTAs, its dynamic shared memory covering the lane's widest image (blur_lane_smem).  The scan
+// kernel takes (argument areas, pointer to the number of jobs, tmax, scratch stride) and runs on
+// a grid of kDdBatch * tmax blocks, tmax = scan_lane_tiles(the lane's largest n).  The image
+// kernel takes one argument, a pointer to the job's argument struct in device memory.
 const void* scan_lane_func();
 uint32_t scan_lane_tiles(uint32_t max_n);
 const void* blur_lane_func();

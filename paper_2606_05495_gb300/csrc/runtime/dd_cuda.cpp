@@ -2,9 +2,10 @@
 //
 // Per lane: a non-blocking stream, an event recorded behind each launch, and one graph built and
 // uploaded once:  WHILE(loop, 1 at each launch) { fetch kernel -> SWITCH(kind) { [0] blur lane
-// kernel, [1] scan lane kernel, [2] image lane kernel } }.  The rings, control lines and completion words live in one
-// page-locked host block mapped into the GPU's address space; the lanes' device blocks (fetched
-// arguments, scan look-back state) in one device allocation.
+// kernel, [1] scan lane kernel (each a batch of up to kDdBatch jobs), [2] image lane kernel } }.
+// The rings, control lines and completion words live in one page-locked host block mapped into
+// the GPU's address space; the lanes' device blocks (fetched arguments, scan look-back state) in
+// one device allocation.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -79,9 +80,9 @@ class CudaDdBackend final : public DdBackend {
       return SET_EINVAL;
     }
     const size_t lane_dev = setk::align256(sizeof(setk::DdLaneDev));
-    // kDdScanBatch look-back areas: scan job j of a batch uses area j
+    // kDdBatch look-back areas: scan job j of a batch uses area j
     scan_stride_ = setk::align256(SL.persist_bytes);
-    const size_t scratch = scan_stride_ * setk::kDdScanBatch;
+    const size_t scratch = scan_stride_ * setk::kDdBatch;
     const size_t img_state = setk::align256(IL.persist_bytes);
     const size_t dev_total = (lane_dev + scratch + img_state) * nl;
     if (cudaMalloc(&dev_block_, dev_total) != cudaSuccess) {
@@ -250,16 +251,16 @@ class CudaDdBackend final : public DdBackend {
     cudaGraphNode_t sn = nullptr;
     DD_CK(cudaGraphAddNode(&sn, body, &fn, nullptr, 1, &sp));
 
-    const void* blur_args = l.dev->args[setk::kDdKindBlur];
-    const void* scan_args = l.dev->scan_args[0];
-    const void* scan_count = &l.dev->scan_count;
+    // the blur and scan nodes read the batch's argument areas and job count
+    const void* batch_args = l.dev->batch_args[0];
+    const void* batch_count = &l.dev->batch_count;
     uint32_t scan_tmax = setk::scan_lane_tiles(cfg_.scan_max_n);
     uint64_t scan_stride = scan_stride_;
-    void* bargs[1] = {&blur_args};
-    void* sargs[4] = {&scan_args, &scan_count, &scan_tmax, &scan_stride};
+    void* bargs[2] = {&batch_args, &batch_count};
+    void* sargs[4] = {&batch_args, &batch_count, &scan_tmax, &scan_stride};
     cudaKernelNodeParams bp{};
     bp.func = const_cast<void*>(setk::blur_lane_func());
-    bp.gridDim = dim3(8);
+    bp.gridDim = dim3(8 * setk::kDdBatch);  // one 8-CTA cluster per job of a batch
     bp.blockDim = dim3(256);
     bp.sharedMemBytes = setk::blur_lane_smem(cfg_.blur_max_w);
     bp.kernelParams = bargs;
@@ -267,7 +268,7 @@ class CudaDdBackend final : public DdBackend {
     DD_CK(cudaGraphAddKernelNode(&bn, sp.conditional.phGraph_out[setk::kDdKindBlur], nullptr, 0, &bp));
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void*>(setk::scan_lane_func());
-    kp.gridDim = dim3(scan_tmax * setk::kDdScanBatch);
+    kp.gridDim = dim3(scan_tmax * setk::kDdBatch);
     kp.blockDim = dim3(256);
     kp.kernelParams = sargs;
     cudaGraphNode_t kn = nullptr;

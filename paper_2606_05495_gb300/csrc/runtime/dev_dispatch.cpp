@@ -7,7 +7,7 @@
 //
 // Submit plans the job's single stage kernel with the same planners as the executor, writes the
 // argument struct into the lane's next ring entry and publishes it with a release store of the
-// entry's sequence word; set_dd_submit_many does this for groups of up to kDdScanBatch
+// entry's sequence word; set_dd_submit_many does this for groups of up to kDdBatch
 // consecutive jobs on one lane (one lane choice and lock per group, sequence words stored last
 // entry first).  Ring entries are reused only after the completion thread has handled
 // the job that used them.  The completion thread reads each lane's done counter, completes the
@@ -61,7 +61,7 @@ class DevDispatch {
  public:
   ~DevDispatch() { release(); }
   set_status init(const set_dd_config& cfg, std::string* err);
-  // Submits a group of up to min(n, kDdScanBatch, ring depth) jobs d[0..) to one lane: the prefix
+  // Submits a group of up to min(n, kDdBatch, ring depth) jobs d[0..) to one lane: the prefix
   // that validates; *n_done = jobs published (their ids *first_id, consecutive).  Returns the
   // first job's error when no job was published, else the error of the job after the group (if
   // one stopped it) or SET_OK.
@@ -223,8 +223,8 @@ set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* firs
   const uint64_t t0 = now_ns();
   // the group: the prefix of d[0..n) that validates and shares d[0]'s SET_F_NONBLOCK, at most the
   // ring's depth; a job that does not validate is reported after the jobs before it are published
-  n = std::min(n, std::min(depth_, setk::kDdScanBatch));
-  setk::JobLayout L[setk::kDdScanBatch];
+  n = std::min(n, std::min(depth_, setk::kDdBatch));
+  setk::JobLayout L[setk::kDdBatch];
   uint32_t g = 0;
   set_status bad = SET_OK;
   std::string why;
@@ -258,8 +258,8 @@ set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* firs
   }
   // ids and argument structs under the lane's lock, so that one submitter's ids stay consecutive
   const uint64_t id0 = next_id_.fetch_add(g);
-  alignas(16) unsigned char args[setk::kDdScanBatch][setk::kDdArgBytes];
-  uint32_t args_size[setk::kDdScanBatch];
+  alignas(16) unsigned char args[setk::kDdBatch][setk::kDdArgBytes];
+  uint32_t args_size[setk::kDdBatch];
   for (uint32_t k = 0; k < g; ++k)
     if (!be_->plan(d[k], id0 + k, li, args[k], &args_size[k])) {
       if (k == 0) return fail(SET_EINVAL, "set_dd: the job does not plan to one kernel with a small argument struct");
@@ -535,7 +535,7 @@ set_status set_dd_submit_many(set_dd* dd, const set_job_desc* jobs, size_t n, ui
   while (k < n) {  // groups of consecutive jobs, one lane each
     uint64_t id = 0;
     uint32_t done = 0;
-    st = dd->dd->submit(&jobs[k], (uint32_t)std::min<size_t>(n - k, setk::kDdScanBatch), &id, &done, &cache);
+    st = dd->dd->submit(&jobs[k], (uint32_t)std::min<size_t>(n - k, setk::kDdBatch), &id, &done, &cache);
     if (done && k == 0 && first_id) *first_id = id;
     k += done;
     if (st != SET_OK) break;

@@ -4,10 +4,11 @@
 // lane's loop starts a host thread that follows the fetch kernel's protocol on the same memory
 // layout: retire the jobs the previous iteration ran (their completion words, then the done
 // counter with release order), poll the next ring entry's sequence word with acquire order for at
-// most idle_us (or until the stop word is set), take the job -- a scan job together with the scan
-// entries directly behind it that are already complete, up to kDdScanBatch, as the fetch kernel
-// does -- and "run" them: wait a seeded random delay and write each trailer {job id, lane, magic},
-// the only bytes of a job it touches.  With no descriptor the loop counts an exit (release order)
+// most idle_us (or until the stop word is set), take the job -- a blur or scan job together with
+// the entries of the same kind directly behind it that are already complete, up to kDdBatch, as
+// the fetch kernel does -- and "run" them: wait a seeded random delay and write each trailer {job
+// id, lane, magic}, the only bytes of a job it touches.  With no descriptor the loop counts an
+// exit (release order)
 // and ends; the backend reports the launch ended only after the thread's last access, as a stream
 // reports a graph complete.
 //
@@ -36,8 +37,8 @@ struct SimLane {
   // state the device keeps across launches (DdLaneDev's fields the protocol uses)
   uint64_t head = 0, cur_first = 0;
   uint32_t cur_count = 0, exits = 0;
-  uint64_t cur_job[setk::kDdScanBatch] = {};
-  set_trailer* cur_trailer[setk::kDdScanBatch] = {};
+  uint64_t cur_job[setk::kDdBatch] = {};
+  set_trailer* cur_trailer[setk::kDdBatch] = {};
   std::thread th;
   std::atomic<bool> running{false};
   std::mt19937_64 rng;
@@ -124,10 +125,10 @@ class SimDdBackend final : public DdBackend {
       uint32_t count = 1;
       l.cur_job[0] = e.job_id;
       l.cur_trailer[0] = e.trailer;
-      if (e.kind == setk::kDdKindScan)
-        for (; count < setk::kDdScanBatch; ++count) {
+      if (e.kind == setk::kDdKindScan || e.kind == setk::kDdKindBlur)
+        for (; count < setk::kDdBatch; ++count) {
           setk::DdEntry& f = ring[(l.head + count) & mask];
-          if (__atomic_load_n(&f.seq, __ATOMIC_ACQUIRE) != want + count || f.kind != setk::kDdKindScan) break;
+          if (__atomic_load_n(&f.seq, __ATOMIC_ACQUIRE) != want + count || f.kind != e.kind) break;
           l.cur_job[count] = f.job_id;
           l.cur_trailer[count] = f.trailer;
         }

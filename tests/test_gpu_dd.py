@@ -275,7 +275,7 @@ def test_image_jobs_of_the_workload_sizes():
 
 def test_queued_scan_jobs_batched_with_ragged_sizes_and_other_kinds():
     # one lane with a deep ring: scan descriptors queue behind the running iteration and the fetch
-    # kernel takes up to kDdScanBatch consecutive ones at once (one launch of the scan node, one
+    # kernel takes up to kDdBatch consecutive ones at once (one launch of the scan node, one
     # scratch area per job); blur and image jobs in between end a batch
     from gpu_util import check_img, img_job
     sizes = [65536, 1, 4097, 30001, 65535, 5, 4096, 8192, 100, 65536, 12289]
@@ -388,3 +388,24 @@ def test_buffer_running_past_its_allocation_is_refused():
     del buf
     check_scan(good)
     check_dd_trailers([good], 1)
+
+
+def test_queued_blur_jobs_batched_in_runs_with_ragged_sizes():
+    # runs of blur jobs of ragged sizes (one 8-CTA cluster each in a batch), broken by scan runs
+    # and image jobs: every batch holds one kind, results exact, trailers their own
+    from gpu_util import check_img, img_job
+    dims = [(256, 256), (1, 1), (17, 3), (255, 257), (64, 1000), (9, 1), (256, 31), (100, 100), (33, 7)]
+    jobs = []
+    for k in range(240):
+        if k % 30 in (12, 13, 14):
+            jobs.append(scan_job(4000 + k, n=(1, 4097, 65536)[k % 3], device=True))
+        elif k % 53 == 52:
+            jobs.append(img_job(4000 + k, dims=(97, 41), device=True))
+        else:
+            W, H = dims[k % len(dims)]
+            jobs.append(blur_job(4000 + k, W=W, H=H, device=True))
+    st, _ = run_dd(jobs, num_lanes=1, ring_depth=64)
+    assert st["completed"] == len(jobs) and st["failed"] == 0 and st["canary_errors"] == 0, st
+    for j in jobs:
+        {1: check_blur, 2: check_scan, 3: check_img}[j.type](j)
+    check_dd_trailers(jobs, 1)

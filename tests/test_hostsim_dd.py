@@ -271,3 +271,33 @@ def test_submit_many_nonblocking_publishes_what_fits(sim):
     assert st.submitted == st.completed == 4 and st.failed == 0
     for k in range(4):
         assert jobs.trailer(k)[0] == first.value + k and jobs.status[k] == B.SET_OK
+
+
+def test_queued_blur_jobs_retire_in_batches(sim):
+    # as the scan case, with blur descriptors: runs of the same kind are taken together
+    os.environ["SET_SIM_DD_DELAY_US"] = "200,400"
+    sim.set_sim_dd_batched_jobs.restype = ctypes.c_uint64
+    before = sim.set_sim_dd_batched_jobs()
+    n = 160
+    dims = B.dims4(64, 32)
+    in_b, out_b = B.set_job_in_bytes(B.SET_JOB_BLUR_HIST, dims), B.set_job_out_bytes(B.SET_JOB_BLUR_HIST, dims)
+    inp = np.zeros(in_b + 64, np.uint8)
+    out = np.zeros((n, out_b + 64), np.uint8)
+    status = (ctypes.c_int32 * n)(*([99] * n))
+    descs = (B.set_job_desc * n)()
+    for k in range(n):
+        d = descs[k]
+        d.type, d.dims, d.in_, d.in_bytes = B.SET_JOB_BLUR_HIST, dims, inp.ctypes.data, in_b
+        d.out, d.out_bytes = out[k].ctypes.data, out_b
+        d.status = ctypes.cast(ctypes.addressof(status) + 4 * k, ctypes.POINTER(ctypes.c_int32))
+    dd = create(sim, num_lanes=1, ring_depth=32)
+    first = ctypes.c_uint64()
+    assert sim.set_dd_submit_many(dd, descs, n, ctypes.byref(first), None) == B.SET_OK
+    assert sim.set_dd_wait_all(dd, 60_000_000) == B.SET_OK
+    st, _ = stats(sim, dd)
+    assert sim.set_dd_destroy(dd) == B.SET_OK
+    assert st.completed == n and st.failed == 0 and st.canary_errors == 0
+    for k in range(n):
+        jid = int(out[k, out_b - 16:out_b - 8].view(np.uint64)[0])
+        assert jid == first.value + k and status[k] == B.SET_OK
+    assert sim.set_sim_dd_batched_jobs() - before >= n // 2
