@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--kernel-only", type=int, default=0, metavar="LAUNCHES",
                    help="only launch the dominant kernel this many times (for ncu), then exit")
-    p.add_argument("--lanes", type=int, default=32, help="device-dispatch arm (set_dd): lanes")
+    p.add_argument("--lanes", type=int, default=64, help="device-dispatch arm (set_dd): lanes")
     p.add_argument("--no-dd-arm", dest="dd_arm", action="store_false",
                    help="leave out the device-dispatch arm (set_dd) of the scan line")
     p.add_argument("--workload", choices=["scan", "blur", "img", "mlp", "serve", "hot", "bind-study", "copy-rates",

@@ -136,9 +136,9 @@ class CudaDdBackend final : public DdBackend {
     return true;
   }
 
-  // device memory of the backend's GPU (the lanes' kernels read and write the buffers in place)
-  // Device memory of the object's GPU; where the driver reports the allocation's range, the whole
-  // buffer must lie inside it, and the range is remembered for the rest of the submit call.
+  // Device memory of the object's GPU (the lanes' kernels read and write the buffers in place);
+  // where the driver reports the allocation's range, the whole buffer must lie inside it, and the
+  // range is remembered for the rest of the submit call.
   bool buffer_ok(const void* p, size_t bytes, DdRangeCache* cache) const override {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
     if (cache && cache->has(a, bytes)) return true;

@@ -284,8 +284,8 @@ set_status DevDispatch::submit(const set_job_desc* d, uint32_t n, uint64_t* firs
     std::memcpy(e.args, args[k], args_size[k]);
   }
   // Publish the group's sequence words last entry first: the lane's fetch waits on the first, and
-  // when it sees it the others are already complete, so queued scan jobs of one group run as one
-  // batch.
+  // when it sees it the others are already complete, so a group's queued blur or scan jobs run as
+  // one batch.
   for (uint32_t k = g; k-- > 0;) __atomic_store_n(&l.m.ring[(s + k) & mask_].seq, s + k + 1, __ATOMIC_RELEASE);
   l.seq.store(s + g, std::memory_order_release);
   uint64_t z = 0;
