@@ -171,3 +171,24 @@ std::unique_ptr<DdBackend> make_dd_backend() { return std::make_unique<SimDdBack
 
 // Test probe: jobs the simulated loops have run in batches of two or more since the library loaded.
 extern "C" uint64_t set_sim_dd_batched_jobs() { return setrt::g_batched_jobs.load(); }
+
+// Test probe: DdRangeCache (the per-call memory of accepted allocations) on fixed cases; returns
+// the bit mask of the cases that came out wrong (0 = all right).
+extern "C" uint32_t set_sim_dd_range_cache_check() {
+  uint32_t bad = 0;
+  setrt::DdRangeCache c;
+  if (c.has(0x1000, 1)) bad |= 1u << 0;  // empty
+  c.add(0x1000, 0x2000);
+  if (!c.has(0x1000, 0x1000)) bad |= 1u << 1;  // the whole allocation
+  if (!c.has(0x1ff0, 0x10)) bad |= 1u << 2;    // ends exactly at its end
+  if (c.has(0x1ff0, 0x11)) bad |= 1u << 3;     // one byte past it
+  if (c.has(0x0fff, 1)) bad |= 1u << 4;        // starts before it
+  if (c.has(0x3000, 0)) bad |= 1u << 5;        // starts past its end (no wrap-around)
+  if (c.has(0x2001, 1)) bad |= 1u << 6;
+  for (uintptr_t k = 1; k <= 4; ++k) c.add(0x10000 * k, 0x10000 * k + 0x100);  // evicts the first
+  if (c.has(0x1000, 1)) bad |= 1u << 7;
+  for (uintptr_t k = 1; k <= 4; ++k)
+    if (!c.has(0x10000 * k + 0x80, 0x80)) bad |= 1u << 8;
+  if (c.n != setrt::DdRangeCache::kN) bad |= 1u << 9;
+  return bad;
+}

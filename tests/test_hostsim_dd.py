@@ -301,3 +301,10 @@ def test_queued_blur_jobs_retire_in_batches(sim):
         jid = int(out[k, out_b - 16:out_b - 8].view(np.uint64)[0])
         assert jid == first.value + k and status[k] == B.SET_OK
     assert sim.set_sim_dd_batched_jobs() - before >= n // 2
+
+
+def test_range_cache_edges(sim):
+    # the per-call memory of accepted device allocations: containment at both ends, no
+    # wrap-around for a start past the end, eviction of the oldest range
+    sim.set_sim_dd_range_cache_check.restype = ctypes.c_uint32
+    assert sim.set_sim_dd_range_cache_check() == 0
