@@ -23,7 +23,8 @@ struct DdLaneMem {
   setk::DdEntry* ring = nullptr;  // `depth` descriptors, written by the host
   setk::DdCtl* ctl = nullptr;     // done counter and loop exits (device), stop flag (host)
   uint32_t* cmpl = nullptr;       // completion word per ring entry (device)
-  void* scan_scratch = nullptr;   // the scan kernel's look-back state (device memory)
+  void* scan_scratch = nullptr;   // the scan kernel's look-back areas, one per job of a batch (device
+                                  // memory); jobs are planned on the first, the kernel adds j * stride
   void* img_state = nullptr;      // the image kernel's ticket and histogram accumulator (device memory)
 };
 
