@@ -382,7 +382,7 @@ set_status CudaDevice::build_graph(Slot& s, uint32_t type, std::string* err) {
   setk::JobLayout L;
   setk::KernelLaunch kl[setk::kMaxKernels];
   int nk = 0;
-  if (!plan(s, rep, &L, kl, &nk)) return SET_OK;  // type not provided by this build: no graph
+  if (!plan(s, rep, &L, kl, &nk)) return SET_OK;  // type without a planner in this library: no graph
   if ((!s.job_mem && L.end > s.bytes) || L.in_bytes > kPlaceholderBytes || L.out_bytes > kPlaceholderBytes)
     return SET_OK;
   uint8_t* base = s.job_mem ? s.job_mem : s.dev;
